@@ -1,0 +1,217 @@
+/*
+ * imgs.h -- C ABI of the B300-native Image-GS rasteriser (libimgs.so).
+ *
+ * Tile-binned differentiable rasterisation of colored, anisotropic 2D
+ * Gaussians (Image-GS, arXiv 2407.01866): per-Gaussian preprocessing and
+ * tile binning, the top-K normalised forward render, its adjoint, the fused
+ * L1 + Adam fit step, random-access decode and the batched fit form.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - All pointers named d_* or documented as "device" are CUDA device
+ *   pointers owned by the caller and only borrowed for the duration of the
+ *   stream-ordered call. The library allocates nothing in these calls, so a
+ *   sequence of them can be captured into a CUDA graph.
+ * - Every call is asynchronous on `stream` unless it says otherwise, and
+ *   returns an igs_status. On failure, igs_last_error() gives a message for
+ *   the calling thread.
+ * - Images are planar float32 [n][H][W], contiguous. Pixel (h, w) is
+ *   evaluated at its centre (w + 1/2, h + 1/2) in pixels; x runs along the
+ *   width, y down the rows.
+ * - A Gaussian is p = (mu, theta, t, c) (Eq. 3 with the inverse scale
+ *   t = 1/s of Sec. 3.3 / Sec. 4.1): mu in [0,1]^2 (Sec. 4.1 maps the image
+ *   to the unit square), theta the rotation angle, t = (t1, t2) inverse
+ *   standard deviations in 1/px along R's columns, c in R^n.
+ *   Covariance Sigma = R S S^T R^T (Eq. 2), S = diag(1/t1, 1/t2).
+ * - A packed parameter / gradient row is (mu_x, mu_y, theta, t1, t2, c0..c_{n-1}).
+ *
+ * Binary32 decisions (fixed here so that any implementation, and the
+ * oracle, selects identical sets). Every operation is rounded once to
+ * nearest-even; fma is a single-rounding fused multiply-add:
+ *   mx = mu_x * W, my = mu_y * H
+ *   c  = round32(cos(theta) in float64), s = round32(sin(theta) in float64)
+ *   T1 = t1*t1, T2 = t2*t2
+ *   A00 = T1*(c*c) + T2*(s*s);  A11 = T1*(s*s) + T2*(c*c)
+ *   A01 = (T1 - T2)*(c*s);      B = A01 + A01
+ *   r = 3 / min(t1, t2)         (3-sigma enclosing circle, Sec. 3.2)
+ *   Tile j = closed rect [X0,X1]x[Y0,Y1], X0 = tile*tx, X1 = min(X0+tile, W):
+ *     ex = max(max(X0 - mx, mx - X1), 0), ey likewise;
+ *     j in S(i)  <=>  ex*ex + ey*ey <= r*r
+ *   Ranking key at (px, py):
+ *     dx = px - mx, dy = py - my, h = fma(B, dy, A00*dx),
+ *     q = fma(h, dx, (A11*dy)*dy)
+ *   The K smallest (q, gaussian index) pairs of S_j are kept (Sec. 3.2,
+ *   Sec. 4.1: K = 10); ties go to the smaller index.
+ * Values (weights, colours, gradients) are float32; the blend is Eq. 5
+ * evaluated as w_k = exp(-(q_k - q_min)/2), c = sum w_k c_k / sum w_k,
+ * which equals Eq. 5 in exact arithmetic. An empty S_j renders 0.
+ */
+#ifndef IMGS_H
+#define IMGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* igs_stream;
+
+typedef enum {
+  IGS_OK = 0,
+  IGS_ERR_INVALID_ARG = 1, /* null pointer, bad size, unsupported K/tile/n */
+  IGS_ERR_ALIGN = 2,       /* a pointer misses its documented alignment */
+  IGS_ERR_CAPACITY = 3,    /* intersections M exceed the workspace capacity */
+  IGS_ERR_CUDA = 4,        /* a CUDA runtime call failed (message has it) */
+  IGS_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+  IGS_ERR_NONFINITE = 6    /* a parameter is NaN/Inf or an inverse scale <= 0 */
+} igs_status;
+
+typedef enum { IGS_F32 = 0, IGS_F16 = 1, IGS_BF16 = 2 } igs_dtype;
+
+/* Device status flags written by kernels into igs_stats.flags. */
+enum { IGS_FLAG_CAPACITY = 1u, IGS_FLAG_NONFINITE = 2u, IGS_FLAG_TIMEOUT = 4u,
+       IGS_FLAG_INTERNAL = 8u /* a list entry out of range (library fault) */ };
+
+/* A borrowed view of N Gaussians (Eq. 3). Each array holds one row per
+ * Gaussian; *_stride is the distance in ELEMENTS between consecutive rows
+ * (xy: >= 2, theta: >= 1, inv_scale: >= 2, color: >= n). All four arrays
+ * have element type `dtype`; alignment: the element size. Device memory. */
+typedef struct {
+  const void* xy;
+  const void* theta;
+  const void* inv_scale;
+  const void* color;
+  int64_t xy_stride, theta_stride, inv_scale_stride, color_stride;
+  int64_t N;
+  int32_t n;      /* channels, 1..32 */
+  int32_t dtype;  /* igs_dtype; F16/BF16 only for preprocess/forward/decode */
+} igs_gaussians;
+
+typedef struct {
+  int32_t K;          /* top-K, one of 1,2,3,4,8,10,16 (Sec. 4.1: 10) */
+  int32_t tile;       /* logical tile edge in px, 8 or 16 (Sec. 4.1: 16);
+                         it changes S_j and therefore the image */
+  /* fit step (Sec. 4.1): Adam learning rates per group */
+  float lr_mu, lr_theta, lr_inv_scale, lr_color;
+  float beta1, beta2, eps;
+  /* clamps after each update (Sec. 3.1): theta, inverse scale, mean */
+  float theta_min, theta_max, t_min, t_max, mu_min, mu_max;
+} igs_config;
+
+/* Host-readable copy of the device status block of one workspace. */
+typedef struct {
+  uint32_t flags;        /* IGS_FLAG_* raised since the last preprocess */
+  uint32_t reserved;
+  int64_t m_needed;      /* intersections M of the last preprocess */
+  int64_t evals;         /* Gaussian-pixel evaluations of one forward:
+                            sum over tiles of |S_j| * pixels(j) */
+  double loss_sum;       /* sum |c_r - c_t| of the last fused backward */
+} igs_stats;
+
+/* Binning result: device pointers into the caller's workspace. Filled by
+ * igs_preprocess_bin; valid until the workspace is reused. */
+typedef struct {
+  int32_t H, W, tile, tiles_x, tiles_y, n;
+  int64_t N, m_capacity;
+  const int32_t* tile_range;  /* [T][2] = [start, end) into list */
+  const int32_t* list;        /* [m_capacity] Gaussian indices grouped by
+                                 tile, ascending within a tile */
+  const float* rec;           /* [N][8] preprocessed geometry (internal) */
+  const float* trig;          /* [N][2] (cos, sin) (internal) */
+  const float* color;         /* [N][n] float32 colours (internal) */
+  void* status;               /* device status block (internal) */
+} igs_bins;
+
+/* Library version: major*10000 + minor*100 + patch. */
+int igs_version(void);
+
+/* Copies the calling thread's last error message (NUL-terminated,
+ * truncated to n bytes). Returns the message length. */
+int igs_last_error(char* buf, size_t n);
+
+/* Defaults of Sec. 4.1: K = 10, 16x16 tiles, learning rates
+ * (mu, colour, inverse scale, theta) = (5e-4, 5e-3, 2e-3, 2e-3), Adam
+ * betas (0.9, 0.999), eps 1e-8; clamps theta in [0, pi], t in [1e-3, 10],
+ * mu in [0, 1]. */
+void igs_default_config(igs_config* cfg);
+
+/* Bytes of device workspace that igs_preprocess_bin needs for N Gaussians
+ * with n channels on an H x W image and room for m_capacity tile-Gaussian
+ * intersections. Host only; no CUDA call. */
+int igs_workspace_size(int64_t N, int32_t n, int32_t H, int32_t W,
+                       const igs_config* cfg, int64_t m_capacity, size_t* bytes);
+
+/* "Project/bin Gaussians to tiles" (Sec. 3.2): per-Gaussian preprocessing
+ * (Eq. 2 inverse covariance, 3-sigma circle), exact tile-circle tests,
+ * per-tile lists by stable key sort and prefix sums. `ws` is a device buffer
+ * of at least igs_workspace_size() bytes, 256-byte aligned. Resets the status
+ * block. If M > m_capacity the lists are truncated and IGS_FLAG_CAPACITY is
+ * raised on the device (no host sync here: read it with igs_read_stats;
+ * m_needed tells the capacity to use). Invalid parameters raise
+ * IGS_FLAG_NONFINITE and that Gaussian is binned nowhere. */
+int igs_preprocess_bin(const igs_gaussians* g, int32_t H, int32_t W,
+                       const igs_config* cfg, void* ws, size_t ws_bytes,
+                       int64_t m_capacity, igs_bins* out, igs_stream stream);
+
+/* Forward render (Eq. 5 with top-K, Sec. 3.2) into d_img [n][H][W] float32
+ * (16-byte aligned). Uses the bins of the same Gaussians. */
+int igs_render_forward(const igs_bins* bins, const igs_config* cfg,
+                       float* d_img, igs_stream stream);
+
+/* Adjoint (Sec. 3.3: gradients through the K retained Gaussians, selection
+ * held fixed). Overwrites d_grad [N][5+n] float32 (packed row order) with
+ * dL/dp. The upstream gradient is d_grad_img [n][H][W] if non-NULL;
+ * otherwise L = mean |c_r - c_t| over H*W*n against d_target [n][H][W]
+ * (d|z|/dz = sign(z), sign(0) = 0) and sum |c_r - c_t| is added to the
+ * status block's loss_sum. Requires float32 parameters. */
+int igs_render_backward(const igs_gaussians* g, const igs_bins* bins,
+                        const igs_config* cfg, const float* d_grad_img,
+                        const float* d_target, float* d_grad, igs_stream stream);
+
+/* Fit state for igs_fit_step: packed float32 parameters and Adam moments,
+ * all [N][5+n] row-major, 16-byte aligned; d_step is a device int32 step
+ * counter (0 before the first step), incremented by each step. */
+typedef struct {
+  float* params;
+  float* grad;
+  float* adam_m;
+  float* adam_v;
+  int32_t* step;
+  int64_t N;
+  int32_t n;
+} igs_fit_state;
+
+/* Adam update of a fit state from its current gradient (Sec. 4.1: Adam
+ * with per-group learning rates; Sec. 3.1: clip theta, scales and means to
+ * their ranges afterwards). Reads st->grad, updates params and moments in
+ * place; uses step = *st->step + 1 for the bias correction and leaves
+ * *st->step unchanged (igs_fit_step advances it). */
+int igs_adam_update(const igs_fit_state* st, const igs_config* cfg, igs_stream stream);
+
+/* One optimisation step (Sec. 3.3, Sec. 4.1): preprocess/bin, fused
+ * forward + L1 + adjoint, Adam with per-group learning rates, clamps. No
+ * host synchronisation; the sequence can be captured in a CUDA graph.
+ * d_loss_out (nullable, device float) receives the step's mean L1 loss. */
+int igs_fit_step(const igs_fit_state* st, const float* d_target, int32_t H,
+                 int32_t W, const igs_config* cfg, void* ws, size_t ws_bytes,
+                 int64_t m_capacity, float* d_loss_out, igs_stream stream);
+
+/* Random-access decode (Sec. 2.2 / abstract: per-pixel decode): colour at
+ * Q arbitrary points d_xy [Q][2] = (x, y) in pixels, written to d_out
+ * [Q][n]. A point belongs to tile (floor(x/tile), floor(y/tile)) clamped to
+ * the grid and is evaluated at (x, y) itself; the rule is the same as the
+ * forward render's. */
+int igs_decode_points(const igs_bins* bins, const igs_config* cfg,
+                      const float* d_xy, int64_t Q, float* d_out, igs_stream stream);
+
+/* Synchronously copies the workspace's status block to *out (this call
+ * synchronises `stream`). */
+int igs_read_stats(const igs_bins* bins, igs_stats* out, igs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IMGS_H */

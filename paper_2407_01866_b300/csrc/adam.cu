@@ -1,0 +1,65 @@
+// Adam update with per-group learning rates and range clamps (Sec. 4.1
+// optimiser and learning rates; Sec. 3.1 clipping of theta and the scales),
+// and the per-step finalisation (step counter, mean loss).
+#include <cmath>
+
+#include "internal.h"
+
+namespace igs {
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_adam(AdamParams a) {
+  __shared__ float s_bc[2];
+  if (threadIdx.x == 0) {
+    const int step = *a.step + 1;
+    s_bc[0] = (float)(1.0 - pow((double)a.b1, (double)step));
+    s_bc[1] = (float)(1.0 - pow((double)a.b2, (double)step));
+  }
+  __syncthreads();
+  const float inv_bc1 = 1.0f / s_bc[0];
+  const float inv_bc2 = 1.0f / s_bc[1];
+  const int np = 5 + a.n;
+  const int64_t total = a.N * np;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int col = (int)(i % np);
+    const float g = a.G[i];
+    const float m = a.b1 * a.m[i] + (1.0f - a.b1) * g;
+    const float v = a.b2 * a.v[i] + (1.0f - a.b2) * g * g;
+    const float lr = col < 2 ? a.lr_mu : col == 2 ? a.lr_theta : col < 5 ? a.lr_t : a.lr_c;
+    float p = a.P[i] - lr * (m * inv_bc1) / (sqrtf(v * inv_bc2) + a.eps);
+    if (col < 2) p = fminf(fmaxf(p, a.mu_min), a.mu_max);
+    else if (col == 2) p = fminf(fmaxf(p, a.theta_min), a.theta_max);
+    else if (col < 5) p = fminf(fmaxf(p, a.t_min), a.t_max);
+    a.P[i] = p;
+    a.m[i] = m;
+    a.v[i] = v;
+  }
+}
+
+__global__ void k_finalize(int32_t* step, DevStatus* st, float inv_count, float* loss_out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *step += 1;
+    if (loss_out) *loss_out = (float)(st->loss_sum * (double)inv_count);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_adam(const AdamParams& a, cudaStream_t s) {
+  const int64_t total = a.N * (5 + a.n);
+  if (total == 0) return cudaSuccess;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  k_adam<<<(unsigned)blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(int32_t* step, DevStatus* status, float inv_count, float* loss_out,
+                            cudaStream_t s) {
+  k_finalize<<<1, 32, 0, s>>>(step, status, inv_count, loss_out);
+  return cudaGetLastError();
+}
+
+}  // namespace igs

@@ -1,0 +1,393 @@
+// Per-Gaussian preprocessing and tile binning (Sec. 3.2: 3-sigma enclosing
+// circles, tile-circle intersection, per-tile sets S_j).
+//
+// Pipeline (all stream-ordered, no host synchronisation, graph-capturable):
+//   k_preprocess   one thread per Gaussian: mu in pixels, inverse covariance
+//                  (Eq. 2), radius 3*max(s), exact count of hit tiles
+//   scan           exclusive prefix sum of the counts -> write offsets, M
+//   k_emit         (tile, gaussian) pairs in Gaussian order
+//   radix sort     stable LSD sort by tile id (8-bit digits): within a tile
+//                  the Gaussians stay in ascending index order, which is the
+//                  tie-break order of the top-K ranking
+//   k_ranges       [start, end) of every tile in the sorted list
+//   k_tile_evals   sum over tiles of |S_j| * pixels(j)
+#include <algorithm>
+
+#include "internal.h"
+
+namespace igs {
+
+namespace {
+
+__device__ __forceinline__ void tile_span(float m, float r, int tile, int tiles, int& lo,
+                                          int& hi) {
+  // One tile of margin each side: membership itself is decided by the exact
+  // circle-rectangle test, the span only has to contain every hit tile.
+  const float inv = 1.0f / (float)tile;  // tile is a power of two: exact
+  float a = floorf((m - r) * inv) - 1.0f;
+  float b = floorf((m + r) * inv) + 1.0f;
+  a = fminf(fmaxf(a, 0.0f), (float)(tiles - 1));
+  b = fminf(fmaxf(b, -1.0f), (float)(tiles - 1));
+  lo = (int)a;
+  hi = (int)b;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_preprocess(PrepParams p) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p.N) return;
+  const T* xy = static_cast<const T*>(p.xy) + i * p.xy_stride;
+  const T* ts = static_cast<const T*>(p.inv_scale) + i * p.inv_scale_stride;
+  const T* cp = static_cast<const T*>(p.color) + i * p.color_stride;
+  const float mux = to_f32(xy[0]), muy = to_f32(xy[1]);
+  const float th = to_f32(static_cast<const T*>(p.theta)[i * p.theta_stride]);
+  const float t1 = to_f32(ts[0]), t2 = to_f32(ts[1]);
+  bool ok = isfinite(mux) && isfinite(muy) && isfinite(th) && isfinite(t1) && isfinite(t2) &&
+            t1 > 0.0f && t2 > 0.0f;
+  bool cok = true;
+  for (int c = 0; c < p.n; ++c) {
+    const float v = to_f32(cp[c]);
+    cok = cok && isfinite(v);
+    p.color_out[i * p.n + c] = v;
+  }
+  if (!(ok && cok)) atomicOr(&p.status->flags, FLAG_NONFINITE);
+
+  const float mx = __fmul_rn(mux, (float)p.W);
+  const float my = __fmul_rn(muy, (float)p.H);
+  double sd, cd;
+  sincos((double)th, &sd, &cd);
+  const float c = __double2float_rn(cd), s = __double2float_rn(sd);
+  float A00, B, A11;
+  conic_from(c, s, t1, t2, A00, B, A11);
+  float r = __fdiv_rn(3.0f, fminf(t1, t2));
+  unsigned int count = 0;
+  if (ok && isfinite(mx) && isfinite(my) && isfinite(r)) {
+    int x0, x1, y0, y1;
+    tile_span(mx, r, p.tile, p.tiles_x, x0, x1);
+    tile_span(my, r, p.tile, p.tiles_y, y0, y1);
+    const float r2 = __fmul_rn(r, r);
+    for (int ty = y0; ty <= y1; ++ty) {
+      const float Y0 = (float)(ty * p.tile), Y1 = (float)min((ty + 1) * p.tile, p.H);
+      for (int tx = x0; tx <= x1; ++tx) {
+        const float X0 = (float)(tx * p.tile), X1 = (float)min((tx + 1) * p.tile, p.W);
+        count += circle_hits_rect(mx, my, r2, X0, X1, Y0, Y1) ? 1u : 0u;
+      }
+    }
+  } else {
+    r = -1.0f;  // binned nowhere
+  }
+  GRec g;
+  g.a = make_float4(mx, my, A00, B);
+  g.b = make_float4(A11, r, t1, t2);
+  p.rec[i] = g;
+  p.trig[i] = make_float2(c, s);
+  p.cnt[i] = count;
+}
+
+__global__ void __launch_bounds__(256) k_emit(PrepParams p) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0 && p.status->m_needed > (unsigned long long)p.m_cap)
+    atomicOr(&p.status->flags, FLAG_CAPACITY);
+  if (i >= p.N) return;
+  const GRec g = p.rec[i];
+  const float mx = g.a.x, my = g.a.y, r = g.b.y;
+  if (!(r >= 0.0f) || !isfinite(mx) || !isfinite(my) || !isfinite(r)) return;
+  unsigned long long pos = p.off[i];
+  int x0, x1, y0, y1;
+  tile_span(mx, r, p.tile, p.tiles_x, x0, x1);
+  tile_span(my, r, p.tile, p.tiles_y, y0, y1);
+  const float r2 = __fmul_rn(r, r);
+  const unsigned long long cap = (unsigned long long)p.m_cap;
+  for (int ty = y0; ty <= y1; ++ty) {
+    const float Y0 = (float)(ty * p.tile), Y1 = (float)min((ty + 1) * p.tile, p.H);
+    for (int tx = x0; tx <= x1; ++tx) {
+      const float X0 = (float)(tx * p.tile), X1 = (float)min((tx + 1) * p.tile, p.W);
+      if (circle_hits_rect(mx, my, r2, X0, X1, Y0, Y1)) {
+        if (pos < cap) {
+          p.keys[pos] = (unsigned int)(ty * p.tiles_x + tx);
+          p.vals[pos] = (unsigned int)i;
+        }
+        ++pos;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- scan
+
+template <typename Out>
+__device__ __forceinline__ Out block_exclusive_scan(Out v, Out* s_warp, Out& block_total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Out incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const Out t = __shfl_up_sync(FULL_MASK, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    Out w = lane < nw ? s_warp[lane] : Out(0);
+    Out wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const Out t = __shfl_up_sync(FULL_MASK, wi, o);
+      if (lane >= o) wi += t;
+    }
+    if (lane < nw) s_warp[lane] = wi - w;
+    if (lane == nw - 1) s_warp[32] = wi;
+  }
+  __syncthreads();
+  const Out res = s_warp[warp] + incl - v;
+  block_total = s_warp[32];
+  __syncthreads();
+  return res;
+}
+
+template <typename In, typename Out>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const In* in, int64_t n,
+                                                              unsigned long long* part) {
+  __shared__ unsigned long long s_warp[33];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_ITEMS;
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+    const int64_t i = base + (int64_t)k * SCAN_THREADS + threadIdx.x;
+    if (i < n) sum += (unsigned long long)in[i];
+  }
+  unsigned long long tot;
+  block_exclusive_scan<unsigned long long>(sum, s_warp, tot);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_partials(unsigned long long* part, int64_t nb,
+                                                        unsigned long long* total) {
+  __shared__ unsigned long long s_warp[33];
+  unsigned long long carry = 0;
+  for (int64_t b0 = 0; b0 < nb; b0 += blockDim.x) {
+    const int64_t b = b0 + threadIdx.x;
+    const unsigned long long v = b < nb ? part[b] : 0ull;
+    unsigned long long tot;
+    const unsigned long long ex = block_exclusive_scan<unsigned long long>(v, s_warp, tot);
+    if (b < nb) part[b] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+template <typename In, typename Out>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const In* in, Out* out, int64_t n,
+                                                            const unsigned long long* part) {
+  __shared__ unsigned long long s_warp[33];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_ITEMS + (int64_t)threadIdx.x * SCAN_PER_THREAD;
+  unsigned long long v[SCAN_PER_THREAD];
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+    const int64_t i = base + k;
+    v[k] = i < n ? (unsigned long long)in[i] : 0ull;
+    sum += v[k];
+  }
+  unsigned long long tot;
+  unsigned long long run = block_exclusive_scan<unsigned long long>(sum, s_warp, tot) +
+                           part[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+    const int64_t i = base + k;
+    if (i < n) out[i] = (Out)run;
+    run += v[k];
+  }
+}
+
+template <typename In, typename Out>
+cudaError_t scan_exclusive(const In* in, Out* out, int64_t n, unsigned long long* part,
+                           unsigned long long* total, cudaStream_t s) {
+  const int64_t nb = (n + SCAN_ITEMS - 1) / SCAN_ITEMS;
+  if (nb == 0) {
+    if (total) return cudaMemsetAsync(total, 0, sizeof(*total), s);
+    return cudaSuccess;
+  }
+  k_scan_reduce<In, Out><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, part);
+  k_scan_partials<<<1, 1024, 0, s>>>(part, nb, total);
+  k_scan_down<In, Out><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, out, n, part);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- radix sort
+
+__device__ __forceinline__ int64_t live_items(const DevStatus* st, int64_t m_cap) {
+  const unsigned long long m = st->m_needed;
+  return m < (unsigned long long)m_cap ? (int64_t)m : m_cap;
+}
+
+__global__ void __launch_bounds__(RADIX_THREADS) k_radix_hist(const unsigned int* keys,
+                                                              const DevStatus* st, int64_t m_cap,
+                                                              int shift, unsigned int* hist,
+                                                              int64_t nblocks) {
+  __shared__ unsigned int cnt[RADIX_DIGITS];
+  for (int d = threadIdx.x; d < RADIX_DIGITS; d += blockDim.x) cnt[d] = 0;
+  __syncthreads();
+  const int64_t M = live_items(st, m_cap);
+  const int64_t base = (int64_t)blockIdx.x * RADIX_ITEMS;
+  if (base < M) {
+#pragma unroll 4
+    for (int k = 0; k < RADIX_PER_THREAD; ++k) {
+      const int64_t i = base + (int64_t)k * RADIX_THREADS + threadIdx.x;
+      if (i < M) atomicAdd(&cnt[(keys[i] >> shift) & (RADIX_DIGITS - 1)], 1u);
+    }
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < RADIX_DIGITS; d += blockDim.x)
+    hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
+}
+
+__global__ void __launch_bounds__(RADIX_THREADS) k_radix_scatter(
+    const unsigned int* keys_in, const unsigned int* vals_in, unsigned int* keys_out,
+    unsigned int* vals_out, const DevStatus* st, int64_t m_cap, int shift,
+    const unsigned int* hist, int64_t nblocks) {
+  constexpr int WARPS = RADIX_THREADS / 32;
+  constexpr int PER_WARP = RADIX_ITEMS / WARPS;  // contiguous items per warp
+  constexpr int ROUNDS = PER_WARP / 32;
+  __shared__ unsigned int wcnt[WARPS][RADIX_DIGITS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t M = live_items(st, m_cap);
+  const int64_t base = (int64_t)blockIdx.x * RADIX_ITEMS;
+  if (base >= M) return;  // whole block idle (uniform)
+  for (int d = lane; d < RADIX_DIGITS; d += 32) wcnt[warp][d] = 0;
+  __syncwarp();
+  const unsigned lt_mask = (1u << lane) - 1u;
+  unsigned int key[ROUNDS], val[ROUNDS];
+  const int64_t wbase = base + (int64_t)warp * PER_WARP;
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    const int64_t i = wbase + r * 32 + lane;
+    const bool valid = i < M;
+    key[r] = valid ? keys_in[i] : 0u;
+    val[r] = valid ? vals_in[i] : 0u;
+    const unsigned d = valid ? ((key[r] >> shift) & (RADIX_DIGITS - 1)) : RADIX_DIGITS;
+    const unsigned peers = __match_any_sync(FULL_MASK, d);
+    if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < RADIX_DIGITS; d += blockDim.x) {
+    unsigned int run = hist[(int64_t)d * nblocks + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < WARPS; ++w) {
+      const unsigned int t = wcnt[w][d];
+      wcnt[w][d] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < ROUNDS; ++r) {
+    const int64_t i = wbase + r * 32 + lane;
+    const bool valid = i < M;
+    const unsigned d = valid ? ((key[r] >> shift) & (RADIX_DIGITS - 1)) : RADIX_DIGITS;
+    const unsigned peers = __match_any_sync(FULL_MASK, d);
+    unsigned int pos = 0;
+    if (valid) pos = wcnt[warp][d] + __popc(peers & lt_mask);
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
+    __syncwarp();
+    if (valid && pos < (unsigned int)M) {
+      keys_out[pos] = key[r];
+      vals_out[pos] = val[r];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- ranges
+
+__global__ void __launch_bounds__(256) k_ranges(const unsigned int* keys, int2* range, int T,
+                                                const DevStatus* st, int64_t m_cap) {
+  const int64_t M = live_items(st, m_cap);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned int k = keys[i];
+    if (k >= (unsigned int)T) continue;
+    if (i == 0 || keys[i - 1] != k) range[k].x = (int)i;
+    if (i == M - 1 || keys[i + 1] != k) range[k].y = (int)(i + 1);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_tile_evals(const int2* range, int T, int H, int W,
+                                                    int tile, int tiles_x, DevStatus* st) {
+  __shared__ unsigned long long s_warp[33];
+  unsigned long long acc = 0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < T; j += gridDim.x * blockDim.x) {
+    const int tx = j % tiles_x, ty = j / tiles_x;
+    const int w = min((tx + 1) * tile, W) - tx * tile;
+    const int h = min((ty + 1) * tile, H) - ty * tile;
+    const int2 r = range[j];
+    acc += (unsigned long long)(r.y - r.x) * (unsigned long long)(w * h);
+  }
+  unsigned long long tot;
+  block_exclusive_scan<unsigned long long>(acc, s_warp, tot);
+  if (threadIdx.x == 0 && tot) atomicAdd(&st->evals, tot);
+}
+
+}  // namespace
+
+cudaError_t launch_preprocess(const PrepParams& p, int dtype, cudaStream_t s) {
+  if (p.N == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((p.N + 255) / 256);
+  switch (dtype) {
+    case 0: k_preprocess<float><<<grid, 256, 0, s>>>(p); break;
+    case 1: k_preprocess<__half><<<grid, 256, 0, s>>>(p); break;
+    case 2: k_preprocess<__nv_bfloat16><<<grid, 256, 0, s>>>(p); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emit(const PrepParams& p, cudaStream_t s) {
+  const unsigned grid = (unsigned)((p.N + 255) / 256);
+  k_emit<<<grid > 0 ? grid : 1, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_u32_to_u64(const unsigned int* in, unsigned long long* out, int64_t n,
+                                   unsigned long long* part, unsigned long long* total,
+                                   cudaStream_t s) {
+  return scan_exclusive<unsigned int, unsigned long long>(in, out, n, part, total, s);
+}
+
+cudaError_t launch_radix_sort(unsigned int* keys0, unsigned int* vals0, unsigned int* keys1,
+                              unsigned int* vals1, unsigned int* hist,
+                              unsigned long long* part, int64_t hist_blocks, int passes,
+                              int64_t m_cap, DevStatus* status, cudaStream_t s,
+                              unsigned int** keys_out, unsigned int** vals_out) {
+  unsigned int* kb[2] = {keys0, keys1};
+  unsigned int* vb[2] = {vals0, vals1};
+  for (int pass = 0; pass < passes; ++pass) {
+    const int shift = pass * RADIX_BITS;
+    const int src = pass & 1, dst = src ^ 1;
+    k_radix_hist<<<(unsigned)hist_blocks, RADIX_THREADS, 0, s>>>(kb[src], status, m_cap, shift,
+                                                                  hist, hist_blocks);
+    cudaError_t e = scan_exclusive<unsigned int, unsigned int>(
+        hist, hist, hist_blocks * RADIX_DIGITS, part, nullptr, s);
+    if (e != cudaSuccess) return e;
+    k_radix_scatter<<<(unsigned)hist_blocks, RADIX_THREADS, 0, s>>>(
+        kb[src], vb[src], kb[dst], vb[dst], status, m_cap, shift, hist, hist_blocks);
+  }
+  *keys_out = kb[passes & 1];
+  *vals_out = vb[passes & 1];
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ranges(const unsigned int* keys, int2* range, int T, int64_t m_cap, int H,
+                          int W, int tile, int tiles_x, DevStatus* status, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(range, 0, sizeof(int2) * (size_t)T, s);
+  if (e != cudaSuccess) return e;
+  int64_t want = (m_cap + 255) / 256;
+  const unsigned grid = (unsigned)(want < 148 * 8 ? (want > 0 ? want : 1) : 148 * 8);
+  k_ranges<<<grid, 256, 0, s>>>(keys, range, T, status, m_cap);
+  const unsigned g2 = (unsigned)std::min<int64_t>((T + 255) / 256, 148 * 4);
+  k_tile_evals<<<g2 > 0 ? g2 : 1, 256, 0, s>>>(range, T, H, W, tile, tiles_x, status);
+  return cudaGetLastError();
+}
+
+}  // namespace igs

@@ -1,0 +1,109 @@
+// Device-side building blocks shared by the rasteriser kernels.
+//
+// The binary32 decision formulas here (conic, 3-sigma radius, tile-circle
+// test, ranking key) are the ones fixed in include/imgs.h. They use the _rn
+// intrinsics so that the compiler cannot contract or reorder them: the
+// selected sets must not depend on code generation.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace igs {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+// 0.5 * log2(e): exp(-x/2) = exp2(-x * HALF_LOG2E)
+constexpr float HALF_LOG2E = 0.72134752044448170368f;
+
+// Preprocessed geometry, two float4 per Gaussian:
+//   a = (mx, my, A00, B = 2*A01), b = (A11, r, t1, t2)
+struct __align__(16) GRec {
+  float4 a;
+  float4 b;
+};
+
+// Device status block at the head of every workspace. The first 32 bytes
+// have the layout of igs_stats in include/imgs.h.
+struct DevStatus {
+  unsigned int flags;
+  unsigned int reserved;
+  unsigned long long m_needed;  // total intersections M
+  unsigned long long evals;     // sum_j |S_j| * pixels(j)
+  double loss_sum;              // sum |c_r - c_t| of the fused backward
+  unsigned int pad[8];
+};
+static_assert(sizeof(DevStatus) == 64, "status block is 64 bytes");
+
+enum : unsigned { FLAG_CAPACITY = 1u, FLAG_NONFINITE = 2u, FLAG_TIMEOUT = 4u, FLAG_INTERNAL = 8u };
+
+template <typename T> __device__ __forceinline__ float to_f32(T v);
+template <> __device__ __forceinline__ float to_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(v); }
+template <> __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) {
+  return __bfloat162float(v);
+}
+
+// Inverse covariance (Eq. 2 inverted) in the header's binary32 sequence.
+__device__ __forceinline__ void conic_from(float c, float s, float t1, float t2,
+                                           float& A00, float& B, float& A11) {
+  const float T1 = __fmul_rn(t1, t1), T2 = __fmul_rn(t2, t2);
+  const float cc = __fmul_rn(c, c), ss = __fmul_rn(s, s), cs = __fmul_rn(c, s);
+  A00 = __fadd_rn(__fmul_rn(T1, cc), __fmul_rn(T2, ss));
+  A11 = __fadd_rn(__fmul_rn(T1, ss), __fmul_rn(T2, cc));
+  const float A01 = __fmul_rn(__fsub_rn(T1, T2), cs);
+  B = __fadd_rn(A01, A01);
+}
+
+// Tile-circle test of Sec. 3.2 on the closed rect [X0,X1]x[Y0,Y1].
+__device__ __forceinline__ bool circle_hits_rect(float mx, float my, float r2, float X0,
+                                                 float X1, float Y0, float Y1) {
+  const float ex = fmaxf(fmaxf(__fsub_rn(X0, mx), __fsub_rn(mx, X1)), 0.0f);
+  const float ey = fmaxf(fmaxf(__fsub_rn(Y0, my), __fsub_rn(my, Y1)), 0.0f);
+  const float d2 = __fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey));
+  return d2 <= r2;
+}
+
+// Ranking key q = d^T Sigma^-1 d at (px, py) (Eq. 1 exponent times -2).
+__device__ __forceinline__ float rank_key(float px, float py, float mx, float my, float A00,
+                                          float B, float A11) {
+  const float dx = __fsub_rn(px, mx);
+  const float dy = __fsub_rn(py, my);
+  const float h = __fmaf_rn(B, dy, __fmul_rn(A00, dx));
+  return __fmaf_rn(h, dx, __fmul_rn(__fmul_rn(A11, dy), dy));
+}
+
+// Sorted insertion of (q, id) into ascending tq[0..K-1] / tid[0..K-1],
+// dropping the largest. Equal keys keep the earlier entry first, so feeding
+// candidates in ascending index order breaks ties toward the smaller index.
+// The K compares are independent; each slot then takes one of three values.
+template <int K>
+__device__ __forceinline__ void topk_insert(float (&tq)[K], int (&tid)[K], float q, int id) {
+  bool b[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) b[k] = q < tq[k];
+#pragma unroll
+  for (int k = K - 1; k >= 1; --k) {
+    const float nq = b[k - 1] ? tq[k - 1] : (b[k] ? q : tq[k]);
+    const int ni = b[k - 1] ? tid[k - 1] : (b[k] ? id : tid[k]);
+    tq[k] = nq;
+    tid[k] = ni;
+  }
+  if (b[0]) {
+    tq[0] = q;
+    tid[0] = id;
+  }
+}
+
+__device__ __forceinline__ float sign_f(float x) {
+  return x > 0.0f ? 1.0f : (x < 0.0f ? -1.0f : 0.0f);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+  return v;
+}
+
+}  // namespace igs

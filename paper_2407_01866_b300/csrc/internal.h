@@ -1,0 +1,109 @@
+// Host-side launchers shared between the C-ABI layer (api.cu) and the kernel
+// translation units. Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace igs {
+
+// Radix sort geometry: one block scatters RADIX_THREADS * RADIX_PER_THREAD keys.
+constexpr int RADIX_THREADS = 256;
+constexpr int RADIX_PER_THREAD = 16;
+constexpr int RADIX_ITEMS = RADIX_THREADS * RADIX_PER_THREAD;
+constexpr int RADIX_BITS = 8;
+constexpr int RADIX_DIGITS = 1 << RADIX_BITS;
+// Scan geometry: one block scans SCAN_THREADS * SCAN_PER_THREAD entries.
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_PER_THREAD = 8;
+constexpr int SCAN_ITEMS = SCAN_THREADS * SCAN_PER_THREAD;
+
+// Byte offsets of the workspace sections (all 256-byte aligned).
+struct WsLayout {
+  size_t status, rec, trig, color, cnt, off, part, keys0, keys1, vals0, vals1, hist, range;
+  size_t total;
+  int64_t hist_blocks;  // radix blocks at full capacity
+  int64_t part_len;     // scan partials entries
+  int tiles_x, tiles_y, passes;
+};
+WsLayout ws_layout(int64_t N, int n, int H, int W, int tile, int64_t m_cap);
+
+struct PrepParams {
+  const void* xy;
+  const void* theta;
+  const void* inv_scale;
+  const void* color;
+  int64_t xy_stride, theta_stride, inv_scale_stride, color_stride;
+  int64_t N;
+  int n, H, W, tile, tiles_x, tiles_y;
+  GRec* rec;
+  float2* trig;
+  float* color_out;
+  unsigned int* cnt;
+  unsigned long long* off;
+  unsigned int* keys;
+  unsigned int* vals;
+  int64_t m_cap;
+  DevStatus* status;
+};
+
+struct RenderParams {
+  const int2* range;   // [T] = [start, end)
+  const int* list;     // gaussian index per intersection
+  const GRec* rec;
+  const float2* trig;
+  const float* color;  // [N][n]
+  int H, W, tiles_x, tiles_y, n;
+  int N;                   // number of Gaussians (bounds guard on list entries)
+  float* img;              // forward output [n][H][W]
+  const float* grad_img;   // backward upstream gradient or null
+  const float* target;     // L1 target when grad_img is null
+  float* grad;             // [N][5+n]
+  float inv_count;         // 1 / (H W n)
+  DevStatus* status;
+  // decode
+  const float* qxy;
+  float* qout;
+  int64_t Q;
+  int tile;
+};
+
+cudaError_t launch_preprocess(const PrepParams& p, int dtype, cudaStream_t s);
+cudaError_t launch_emit(const PrepParams& p, cudaStream_t s);
+// Exclusive scan of n u32 counts into u64 offsets; total goes to *total.
+cudaError_t launch_scan_u32_to_u64(const unsigned int* in, unsigned long long* out, int64_t n,
+                                   unsigned long long* part, unsigned long long* total,
+                                   cudaStream_t s);
+cudaError_t launch_radix_sort(unsigned int* keys0, unsigned int* vals0, unsigned int* keys1,
+                              unsigned int* vals1, unsigned int* hist,
+                              unsigned long long* part, int64_t hist_blocks, int passes,
+                              int64_t m_cap, DevStatus* status, cudaStream_t s,
+                              unsigned int** keys_out, unsigned int** vals_out);
+cudaError_t launch_ranges(const unsigned int* keys, int2* range, int T, int64_t m_cap,
+                          int H, int W, int tile, int tiles_x, DevStatus* status,
+                          cudaStream_t s);
+
+// Render family: return cudaErrorInvalidValue for an unsupported (tile, K, n).
+cudaError_t launch_render_fwd(const RenderParams& p, int tile, int K, cudaStream_t s);
+cudaError_t launch_render_bwd(const RenderParams& p, int tile, int K, cudaStream_t s);
+cudaError_t launch_decode(const RenderParams& p, int K, cudaStream_t s);
+bool render_supported(int tile, int K, int n);
+
+struct AdamParams {
+  float* P;
+  const float* G;
+  float* m;
+  float* v;
+  int32_t* step;
+  int64_t N;
+  int n;
+  float lr_mu, lr_theta, lr_t, lr_c, b1, b2, eps;
+  float theta_min, theta_max, t_min, t_max, mu_min, mu_max;
+};
+cudaError_t launch_adam(const AdamParams& a, cudaStream_t s);
+cudaError_t launch_finalize(int32_t* step, DevStatus* status, float inv_count, float* loss_out,
+                            cudaStream_t s);
+
+}  // namespace igs

@@ -1,0 +1,276 @@
+"""ctypes binding of libimgs.so (include/imgs.h), with a torch.autograd wrapper.
+
+Argument marshalling only: every step of the rasteriser runs in the CUDA
+library. PyTorch supplies device memory and the current stream. There is no
+CPU fallback: if the library is missing or cannot be loaded, every call raises.
+"""
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libimgs.so")
+
+IGS_OK, IGS_ERR_INVALID_ARG, IGS_ERR_ALIGN, IGS_ERR_CAPACITY, IGS_ERR_CUDA, \
+    IGS_ERR_TIMEOUT, IGS_ERR_NONFINITE = range(7)
+IGS_F32, IGS_F16, IGS_BF16 = 0, 1, 2
+FLAG_CAPACITY, FLAG_NONFINITE, FLAG_TIMEOUT = 1, 2, 4
+
+_DTYPE = {torch.float32: IGS_F32, torch.float16: IGS_F16, torch.bfloat16: IGS_BF16}
+
+
+class IgsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libimgs error {code}: {msg}")
+        self.code = code
+
+
+class Gaussians(ctypes.Structure):
+    _fields_ = [("xy", ctypes.c_void_p), ("theta", ctypes.c_void_p),
+                ("inv_scale", ctypes.c_void_p), ("color", ctypes.c_void_p),
+                ("xy_stride", ctypes.c_int64), ("theta_stride", ctypes.c_int64),
+                ("inv_scale_stride", ctypes.c_int64), ("color_stride", ctypes.c_int64),
+                ("N", ctypes.c_int64), ("n", ctypes.c_int32), ("dtype", ctypes.c_int32)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("lr_mu", ctypes.c_float), ("lr_theta", ctypes.c_float),
+                ("lr_inv_scale", ctypes.c_float), ("lr_color", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("theta_min", ctypes.c_float), ("theta_max", ctypes.c_float),
+                ("t_min", ctypes.c_float), ("t_max", ctypes.c_float),
+                ("mu_min", ctypes.c_float), ("mu_max", ctypes.c_float)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("m_needed", ctypes.c_int64), ("evals", ctypes.c_int64),
+                ("loss_sum", ctypes.c_double)]
+
+
+class Bins(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("tiles_x", ctypes.c_int32), ("tiles_y", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("N", ctypes.c_int64), ("m_capacity", ctypes.c_int64),
+                ("tile_range", ctypes.c_void_p), ("list", ctypes.c_void_p),
+                ("rec", ctypes.c_void_p), ("trig", ctypes.c_void_p),
+                ("color", ctypes.c_void_p), ("status", ctypes.c_void_p)]
+
+
+class FitState(ctypes.Structure):
+    _fields_ = [("params", ctypes.c_void_p), ("grad", ctypes.c_void_p),
+                ("adam_m", ctypes.c_void_p), ("adam_v", ctypes.c_void_p),
+                ("step", ctypes.c_void_p), ("N", ctypes.c_int64), ("n", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "igs_version": ([], ctypes.c_int),
+    "igs_last_error": ([ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
+    "igs_default_config": ([ctypes.POINTER(Config)], None),
+    "igs_workspace_size": ([ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                            ctypes.POINTER(Config), ctypes.c_int64,
+                            ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "igs_preprocess_bin": ([ctypes.POINTER(Gaussians), ctypes.c_int32, ctypes.c_int32,
+                            ctypes.POINTER(Config), _P, ctypes.c_size_t, ctypes.c_int64,
+                            ctypes.POINTER(Bins), _P], ctypes.c_int),
+    "igs_render_forward": ([ctypes.POINTER(Bins), ctypes.POINTER(Config), _P, _P], ctypes.c_int),
+    "igs_render_backward": ([ctypes.POINTER(Gaussians), ctypes.POINTER(Bins),
+                             ctypes.POINTER(Config), _P, _P, _P, _P], ctypes.c_int),
+    "igs_fit_step": ([ctypes.POINTER(FitState), _P, ctypes.c_int32, ctypes.c_int32,
+                      ctypes.POINTER(Config), _P, ctypes.c_size_t, ctypes.c_int64, _P, _P],
+                     ctypes.c_int),
+    "igs_adam_update": ([ctypes.POINTER(FitState), ctypes.POINTER(Config), _P], ctypes.c_int),
+    "igs_decode_points": ([ctypes.POINTER(Bins), ctypes.POINTER(Config), _P, ctypes.c_int64,
+                           _P, _P], ctypes.c_int),
+    "igs_read_stats": ([ctypes.POINTER(Bins), ctypes.POINTER(Stats), _P], ctypes.c_int),
+}
+
+_lib = None
+
+
+def load():
+    """Load libimgs.so once; raises if it is missing (there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2407_01866_b300.build`")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+    return _lib
+
+
+def exported_names():
+    return list(_SIGNATURES)
+
+
+def _check(code):
+    if code != IGS_OK:
+        buf = ctypes.create_string_buffer(1024)
+        load().igs_last_error(buf, 1024)
+        raise IgsError(code, buf.value.decode())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def default_config(**overrides):
+    c = Config()
+    load().igs_default_config(ctypes.byref(c))
+    for k, v in overrides.items():
+        setattr(c, k, v)
+    return c
+
+
+def version():
+    return load().igs_version()
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("tensors must be CUDA tensors")
+
+
+def gaussians_view(xy, theta, inv_scale, color):
+    """igs_gaussians over four tensors of one dtype (rows may be strided views)."""
+    _require_cuda(xy, theta, inv_scale, color)
+    dt = _DTYPE[xy.dtype]
+    for t in (theta, inv_scale, color):
+        if t.dtype != xy.dtype:
+            raise ValueError("all parameter tensors must share one dtype")
+    N = xy.shape[0]
+    n = color.shape[1]
+    if xy.stride(1) != 1 or inv_scale.stride(1) != 1 or color.stride(1) != 1:
+        raise ValueError("parameter rows must be contiguous")
+    g = Gaussians(xy.data_ptr(), theta.data_ptr(), inv_scale.data_ptr(), color.data_ptr(),
+                  xy.stride(0), theta.stride(0), inv_scale.stride(0), color.stride(0), N, n, dt)
+    return g
+
+
+def packed_view(P, n):
+    """igs_gaussians over a packed [N, 5+n] tensor (mu_x, mu_y, theta, t1, t2, c...)."""
+    return gaussians_view(P[:, 0:2], P[:, 2], P[:, 3:5], P[:, 5:5 + n])
+
+
+def workspace_size(N, n, H, W, cfg, m_capacity):
+    b = ctypes.c_size_t(0)
+    _check(load().igs_workspace_size(N, n, H, W, ctypes.byref(cfg), m_capacity, ctypes.byref(b)))
+    return b.value
+
+
+def alloc_workspace(nbytes, device=None):
+    # torch's caching allocator returns 512-byte aligned blocks
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8,
+                       device=device or torch.device("cuda"))
+
+
+def preprocess_bin(g, H, W, cfg, ws, m_capacity, stream=None):
+    bins = Bins()
+    _check(load().igs_preprocess_bin(ctypes.byref(g), H, W, ctypes.byref(cfg), _ptr(ws),
+                                     ws.numel(), m_capacity, ctypes.byref(bins), _stream(stream)))
+    return bins
+
+
+def render_forward(bins, cfg, img, stream=None):
+    _check(load().igs_render_forward(ctypes.byref(bins), ctypes.byref(cfg), _ptr(img),
+                                     _stream(stream)))
+
+
+def render_backward(g, bins, cfg, grad_img, target, grad, stream=None):
+    _check(load().igs_render_backward(ctypes.byref(g), ctypes.byref(bins), ctypes.byref(cfg),
+                                      _ptr(grad_img), _ptr(target), _ptr(grad), _stream(stream)))
+
+
+def fit_step(state, target, H, W, cfg, ws, m_capacity, loss_out=None, stream=None):
+    _check(load().igs_fit_step(ctypes.byref(state), _ptr(target), H, W, ctypes.byref(cfg),
+                               _ptr(ws), ws.numel(), m_capacity, _ptr(loss_out), _stream(stream)))
+
+
+def adam_update(state, cfg, stream=None):
+    _check(load().igs_adam_update(ctypes.byref(state), ctypes.byref(cfg), _stream(stream)))
+
+
+def decode_points(bins, cfg, xy, out, stream=None):
+    _check(load().igs_decode_points(ctypes.byref(bins), ctypes.byref(cfg), _ptr(xy),
+                                    xy.shape[0], _ptr(out), _stream(stream)))
+
+
+def read_stats(bins, stream=None):
+    st = Stats()
+    _check(load().igs_read_stats(ctypes.byref(bins), ctypes.byref(st), _stream(stream)))
+    return st
+
+
+# ---------------------------------------------------------------------------
+# Convenience layer: sized workspaces and an autograd function.
+# ---------------------------------------------------------------------------
+
+class Binner:
+    """Owns a workspace sized for (N, n, H, W) and grows its intersection
+    capacity when a binning reports that it overflowed."""
+
+    def __init__(self, N, n, H, W, cfg=None, m_capacity=None, headroom=1.5):
+        self.N, self.n, self.H, self.W = N, n, H, W
+        self.cfg = cfg or default_config()
+        self.headroom = headroom
+        self.m_capacity = int(m_capacity or max(1024, 8 * N))
+        self._alloc()
+
+    def _alloc(self):
+        self.ws = alloc_workspace(workspace_size(self.N, self.n, self.H, self.W, self.cfg,
+                                                 self.m_capacity))
+
+    def bin(self, g, stream=None, check=True):
+        """Bin g; with check=True, synchronises and re-bins with a larger
+        capacity if the intersections did not fit."""
+        bins = preprocess_bin(g, self.H, self.W, self.cfg, self.ws, self.m_capacity, stream)
+        if check:
+            st = read_stats(bins, stream)
+            if st.flags & FLAG_CAPACITY:
+                self.m_capacity = int(st.m_needed * self.headroom) + 1024
+                self._alloc()
+                bins = preprocess_bin(g, self.H, self.W, self.cfg, self.ws, self.m_capacity,
+                                      stream)
+        return bins
+
+
+class _RenderFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, xy, theta, inv_scale, color, H, W, cfg):
+        g = gaussians_view(xy, theta, inv_scale, color)
+        binner = Binner(g.N, g.n, H, W, cfg)
+        bins = binner.bin(g)
+        img = torch.empty((g.n, H, W), dtype=torch.float32, device=xy.device)
+        render_forward(bins, cfg, img)
+        ctx.save_for_backward(xy, theta, inv_scale, color)
+        ctx.keep = (binner, bins, cfg, H, W)
+        return img
+
+    @staticmethod
+    def backward(ctx, grad_img):
+        xy, theta, inv_scale, color = ctx.saved_tensors
+        binner, bins, cfg, H, W = ctx.keep
+        g = gaussians_view(xy, theta, inv_scale, color)
+        n = color.shape[1]
+        grad = torch.empty((xy.shape[0], 5 + n), dtype=torch.float32, device=xy.device)
+        render_backward(g, bins, cfg, grad_img.contiguous().float(), None, grad)
+        return (grad[:, 0:2], grad[:, 2], grad[:, 3:5], grad[:, 5:], None, None, None)
+
+
+def render(xy, theta, inv_scale, color, H, W, cfg=None):
+    """Differentiable render (Eq. 5) -> planar float32 [n, H, W]."""
+    return _RenderFn.apply(xy, theta, inv_scale, color, H, W, cfg or default_config())

@@ -1,0 +1,182 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: tile lists and top-K selections are integer results and must be
+identical; pixels within 1e-5 max abs (FP32 path); gradients within 1e-3
+normwise relative error per parameter group.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import image_gs as O  # noqa: E402
+from paper_2407_01866_b300 import lib as L  # noqa: E402
+from paper_2407_01866_b300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from gpu_harness import GpuSet, grad_rel_error  # noqa: E402
+
+PIX_TOL = 1e-5
+GRAD_TOL = 1e-3
+
+
+def oset(N, n, seed, s_range=(0.5, 8.0)):
+    d = synth.gaussians(N, n, seed, s_range=s_range)
+    return O.Gaussians(d["xy"], d["theta"], d["inv_scale"], d["color"])
+
+
+CASES = [
+    # (H, W, N, n, K, tile, seed, s_range)
+    (256, 256, 4096, 3, 10, 16, 0, (0.5, 8.0)),     # the 256^2 RGB workload
+    (37, 53, 300, 1, 3, 8, 1, (0.5, 8.0)),          # ragged tiles, 8x8 tiles
+    (70, 45, 400, 4, 16, 16, 2, (0.5, 6.0)),
+    (48, 64, 250, 9, 10, 16, 3, (0.5, 8.0)),
+    (40, 40, 200, 5, 4, 8, 4, (0.5, 8.0)),          # generic channel count
+    (64, 64, 1500, 2, 8, 16, 5, (8.0, 30.0)),       # |S_j| > shared-memory slots
+    (33, 17, 60, 3, 1, 16, 6, (0.5, 8.0)),
+    (16, 16, 1, 3, 10, 16, 7, (0.5, 8.0)),          # single Gaussian
+    (1, 1, 5, 3, 2, 8, 8, (0.5, 8.0)),              # one pixel
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}_N{c[2]}_n{c[3]}_K{c[4]}_t{c[5]}")
+def test_tile_lists_equal_oracle_sets(case):
+    H, W, N, n, K, tile, seed, sr = case
+    g = oset(N, n, seed, sr)
+    gs = GpuSet(g, H, W, K, tile)
+    want = O.tile_lists(g, H, W, tile)
+    got = gs.tile_lists()
+    assert len(got) == len(want)
+    for j, (a, b) in enumerate(zip(got, want)):
+        np.testing.assert_array_equal(a, b, err_msg=f"tile {j}")
+    assert gs.stats.m_needed == sum(len(w) for w in want)
+    assert gs.stats.evals == O.count_evals(g, H, W, tile)
+    assert gs.stats.flags == 0
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}_N{c[2]}_n{c[3]}_K{c[4]}_t{c[5]}")
+def test_forward_matches_oracle(case):
+    H, W, N, n, K, tile, seed, sr = case
+    g = oset(N, n, seed, sr)
+    gs = GpuSet(g, H, W, K, tile)
+    got = gs.forward()
+    want = O.render_image(g, H, W, K=K, tile=tile)
+    err = np.abs(got - want).max()
+    assert err <= PIX_TOL, err
+
+
+@pytest.mark.parametrize("case", CASES[:7], ids=lambda c: f"{c[0]}x{c[1]}_N{c[2]}_n{c[3]}_K{c[4]}_t{c[5]}")
+def test_backward_with_upstream_gradient_matches_oracle(case):
+    H, W, N, n, K, tile, seed, sr = case
+    g = oset(N, n, seed, sr)
+    gs = GpuSet(g, H, W, K, tile)
+    gimg = np.random.default_rng(seed + 100).standard_normal((n, H, W)).astype(np.float32)
+    got, _ = gs.backward(grad_img=gimg)
+    want = O.backward_image(g, gimg, H, W, K=K, tile=tile)
+    errs = grad_rel_error(got, want)
+    assert max(errs.values()) <= GRAD_TOL, errs
+
+
+def _unambiguous_target(g, H, W, K, tile, seed, margin=1e-4):
+    """Synthetic target moved away from the oracle's image wherever |c_r - c_t|
+    is within `margin`, so that sign(c_r - c_t) has one correct value."""
+    t = synth.target_image(H, W, g.n, seed=seed).astype(np.float64)
+    img = O.render_image(g, H, W, K=K, tile=tile)
+    close = np.abs(img - t) < margin
+    t[close] = img[close] + np.where(t[close] >= img[close], margin, -margin)
+    t = t.astype(np.float32)
+    assert np.abs(img - t.astype(np.float64)).min() >= margin * 0.5
+    return t, img
+
+
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[3], CASES[5]],
+                         ids=lambda c: f"{c[0]}x{c[1]}_N{c[2]}_n{c[3]}")
+def test_fused_l1_loss_and_gradient_match_oracle(case):
+    H, W, N, n, K, tile, seed, sr = case
+    g = oset(N, n, seed, sr)
+    target, img = _unambiguous_target(g, H, W, K, tile, seed)
+    gs = GpuSet(g, H, W, K, tile)
+    got, st = gs.backward(target=target)
+    loss, dimg = O.l1_loss(img, target)
+    want = O.backward_image(g, dimg, H, W, K=K, tile=tile)
+    assert abs(st.loss_sum / (H * W * n) - loss) <= 1e-6
+    errs = grad_rel_error(got, want)
+    assert max(errs.values()) <= GRAD_TOL, errs
+
+
+def test_decode_random_points_match_oracle():
+    H, W, N, n = 256, 256, 4096, 3
+    g = oset(N, n, 0)
+    gs = GpuSet(g, H, W)
+    pts = synth.query_points(5000, H, W, seed=3)
+    pts = np.concatenate([pts, O.pixel_centres(synth.sample_pixels(500, H, W, 4)).astype(np.float32),
+                          np.array([[0, 0], [W - 1e-3, H - 1e-3], [W - 1e-3, 0]], np.float32)])
+    got = gs.decode(pts)
+    want = O.render_points(g, pts.astype(np.float64), H, W)
+    assert np.abs(got - want).max() <= PIX_TOL
+    # decoding a pixel centre equals the rendered pixel
+    img = gs.forward()
+    pix = synth.sample_pixels(300, H, W, 5)
+    cen = O.pixel_centres(pix).astype(np.float32)
+    np.testing.assert_array_equal(gs.decode(cen), img[:, pix[:, 0], pix[:, 1]].T)
+
+
+@pytest.mark.parametrize("dt", ["float16", "bfloat16"])
+def test_half_precision_storage_forward_and_decode(dt):
+    H, W, N, n = 128, 160, 2000, 3
+    d = synth.gaussians(N, n, 11)
+    tdt = getattr(torch, dt)
+    # the oracle evaluates the exact upcast of the stored half values
+    half = {k: torch.from_numpy(v).to(tdt).float().numpy() for k, v in d.items()}
+    g = O.Gaussians(half["xy"], half["theta"], half["inv_scale"], half["color"])
+    gs = GpuSet(g, H, W, dtype=tdt)
+    got = gs.forward()
+    want = O.render_image(g, H, W)
+    err = np.abs(got - want).max()
+    assert err <= 2e-3 and err <= PIX_TOL, err
+    pts = synth.query_points(2000, H, W, seed=1)
+    assert np.abs(gs.decode(pts) - O.render_points(g, pts.astype(np.float64), H, W)).max() <= PIX_TOL
+
+
+def test_empty_set_and_empty_tiles_render_zero():
+    g = O.Gaussians(np.zeros((0, 2)), np.zeros(0), np.zeros((0, 2)), np.zeros((0, 3)))
+    gs = GpuSet(g, 40, 24)
+    assert not gs.forward().any()
+    assert gs.stats.m_needed == 0
+    g1 = O.Gaussians([[0.1, 0.1]], [0.0], [[2.0, 2.0]], [[1.0, 2.0, 3.0]])
+    gs1 = GpuSet(g1, 64, 64)
+    img = gs1.forward()
+    np.testing.assert_array_equal(img[:, 16:, :], 0)
+    np.testing.assert_array_equal(img[:, :16, :16], np.broadcast_to(np.array([1.0, 2.0, 3.0])[:, None, None], (3, 16, 16)))
+
+
+def test_capacity_overflow_is_flagged_and_recovered():
+    H, W, N, n = 128, 128, 2000, 3
+    g = oset(N, n, 12)
+    gs = GpuSet(g, H, W, m_capacity=64)            # grows after the first binning
+    assert gs.binner.m_capacity > 64
+    np.testing.assert_allclose(gs.forward(), O.render_image(g, H, W), atol=PIX_TOL)
+    v = gs.view
+    small = L.preprocess_bin(v, H, W, gs.cfg, L.alloc_workspace(
+        L.workspace_size(N, n, H, W, gs.cfg, 64)), 64)
+    st = L.read_stats(small)
+    assert st.flags & L.FLAG_CAPACITY and st.m_needed == gs.stats.m_needed
+
+
+def test_nonfinite_parameters_are_flagged_and_skipped():
+    H, W = 48, 48
+    g = oset(50, 3, 13)
+    g.inv_scale[3, 0] = -1.0
+    g.xy[7, 1] = np.nan
+    gs = GpuSet(g, H, W)
+    assert gs.stats.flags & L.FLAG_NONFINITE
+    lists = gs.tile_lists()
+    assert all(3 not in l and 7 not in l for l in lists)
+    keep = np.setdiff1d(np.arange(50), [3, 7])
+    gk = O.Gaussians(g.xy[keep], g.theta[keep], g.inv_scale[keep], g.color[keep])
+    want = O.render_image(gk, H, W)
+    np.testing.assert_allclose(gs.forward(), want, atol=PIX_TOL)
