@@ -96,7 +96,8 @@ typedef struct {
                          it changes S_j and therefore the image */
   /* fit step (Sec. 4.1): Adam learning rates per group */
   float lr_mu, lr_theta, lr_inv_scale, lr_color;
-  float beta1, beta2, eps;
+  double beta1, beta2;  /* double: 0.999 in float32 would move 1-beta2 by 1.3e-5 */
+  float eps;
   /* clamps after each update (Sec. 3.1): theta, inverse scale, mean */
   float theta_min, theta_max, t_min, t_max, mu_min, mu_max;
 } igs_config;

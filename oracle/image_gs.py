@@ -63,7 +63,7 @@ class Gaussians:
         self.theta = np.ascontiguousarray(np.asarray(theta, dtype=F32).reshape(-1))
         self.inv_scale = np.ascontiguousarray(np.asarray(inv_scale, dtype=F32).reshape(-1, 2))
         c = np.asarray(color, dtype=F32)
-        self.color = np.ascontiguousarray(c.reshape(c.shape[0], -1))
+        self.color = np.ascontiguousarray(c.reshape(c.shape[0], c.shape[1] if c.ndim > 1 else 1))
         self.N = self.xy.shape[0]
         self.n = self.color.shape[1]
         assert self.theta.shape[0] == self.N and self.inv_scale.shape[0] == self.N

@@ -13,8 +13,8 @@ __global__ void __launch_bounds__(256) k_adam(AdamParams a) {
   __shared__ float s_bc[2];
   if (threadIdx.x == 0) {
     const int step = *a.step + 1;
-    s_bc[0] = (float)(1.0 - pow((double)a.b1, (double)step));
-    s_bc[1] = (float)(1.0 - pow((double)a.b2, (double)step));
+    s_bc[0] = (float)(1.0 - pow(a.b1d, (double)step));
+    s_bc[1] = (float)(1.0 - pow(a.b2d, (double)step));
   }
   __syncthreads();
   const float inv_bc1 = 1.0f / s_bc[0];
@@ -25,8 +25,8 @@ __global__ void __launch_bounds__(256) k_adam(AdamParams a) {
        i += (int64_t)gridDim.x * blockDim.x) {
     const int col = (int)(i % np);
     const float g = a.G[i];
-    const float m = a.b1 * a.m[i] + (1.0f - a.b1) * g;
-    const float v = a.b2 * a.v[i] + (1.0f - a.b2) * g * g;
+    const float m = a.b1 * a.m[i] + a.omb1 * g;
+    const float v = a.b2 * a.v[i] + a.omb2 * g * g;
     const float lr = col < 2 ? a.lr_mu : col == 2 ? a.lr_theta : col < 5 ? a.lr_t : a.lr_c;
     float p = a.P[i] - lr * (m * inv_bc1) / (sqrtf(v * inv_bc2) + a.eps);
     if (col < 2) p = fminf(fmaxf(p, a.mu_min), a.mu_max);

@@ -169,8 +169,8 @@ void igs_default_config(igs_config* c) {
   c->lr_color = 5e-3f;
   c->lr_inv_scale = 2e-3f;
   c->lr_theta = 2e-3f;
-  c->beta1 = 0.9f;
-  c->beta2 = 0.999f;
+  c->beta1 = 0.9;
+  c->beta2 = 0.999;
   c->eps = 1e-8f;
   c->theta_min = 0.0f;
   c->theta_max = 3.14159265358979323846f;
@@ -330,8 +330,12 @@ int igs_adam_update(const igs_fit_state* st, const igs_config* cfg, igs_stream s
   a.lr_theta = cfg->lr_theta;
   a.lr_t = cfg->lr_inv_scale;
   a.lr_c = cfg->lr_color;
-  a.b1 = cfg->beta1;
-  a.b2 = cfg->beta2;
+  a.b1 = (float)cfg->beta1;
+  a.b2 = (float)cfg->beta2;
+  a.omb1 = (float)(1.0 - cfg->beta1);
+  a.omb2 = (float)(1.0 - cfg->beta2);
+  a.b1d = cfg->beta1;
+  a.b2d = cfg->beta2;
   a.eps = cfg->eps;
   a.theta_min = cfg->theta_min;
   a.theta_max = cfg->theta_max;

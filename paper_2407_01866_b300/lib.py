@@ -38,7 +38,7 @@ class Config(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("lr_mu", ctypes.c_float), ("lr_theta", ctypes.c_float),
                 ("lr_inv_scale", ctypes.c_float), ("lr_color", ctypes.c_float),
-                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_float),
                 ("theta_min", ctypes.c_float), ("theta_max", ctypes.c_float),
                 ("t_min", ctypes.c_float), ("t_max", ctypes.c_float),
                 ("mu_min", ctypes.c_float), ("mu_max", ctypes.c_float)]
