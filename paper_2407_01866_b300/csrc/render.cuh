@@ -3,18 +3,24 @@
 // loss, and random-access decode. Included by the translation units that
 // instantiate and dispatch them.
 //
-// One CTA renders one logical tile (TILE x TILE pixels, one pixel per
-// thread). The tile's list S_j is staged through shared memory in chunks of
-// TILE*TILE Gaussians; every pixel ranks each candidate by its binary32 key q
-// and keeps the K smallest in registers. The insertion network runs only
-// when some lane of the warp improves on its current K-th key (warp vote),
-// so the common reject costs one compare. Colours of the K winners are read
-// once at the end (the blend needs only the K winners).
+// One CTA renders one logical tile of TILE x TILE pixels, one pixel per
+// thread; each warp owns a compact 8 x 4 block so that its pixels share
+// most of their winners. The tile's list S_j (ascending Gaussian index) is
+// staged through shared memory in chunks of TILE*TILE records.
 //
-// The adjoint recomputes the selection and the weights (nothing is stored
-// between forward and backward), forms dL/dq for each winner and reduces the
-// per-pixel contributions of the tile in shared memory, one slot per list
-// position, before one global atomic per (tile, Gaussian, parameter).
+//   pass A  keys only: every pixel keeps its K smallest ranking keys q with a
+//           min/max insertion network, run only when some lane of the warp
+//           improves on its K-th key (warp vote). Gives q_min and the
+//           threshold tau = K-th smallest key.
+//   pass B  list order: a candidate is a winner iff q < tau, or q == tau
+//           while equal-key slots remain (K minus the keys below tau), which
+//           is exactly the top-K of the (q, index) order. Winners are blended
+//           with w = exp(-(q - q_min)/2) (Eq. 5).
+//   pass C  (adjoint only) candidate-major: threads own (candidate, group of
+//           pixels), re-test membership exactly from each pixel's (tau,
+//           position of its last tau-valued winner), and accumulate dL/dq
+//           moments in registers; one reduction and 5+n global atomics per
+//           (tile, Gaussian). Nothing is stored between forward and adjoint.
 #pragma once
 #include "internal.h"
 
@@ -28,77 +34,128 @@ __device__ __forceinline__ int nchan(const RenderParams& p) {
   return NC > 0 ? NC : p.n;
 }
 
-// Shared-memory gradient slots for the adjoint (one row of 5+n floats per
-// list position); positions beyond the capacity use global atomics.
-template <int NC> struct AccCap {
-  static constexpr int NP = 5 + Chan<NC>::R;
-  static constexpr int L = ((8192 / NP) / 32) * 32;
-};
+// Local (x, y) of the pixel owned by thread t: warp w covers an 8 x 4 block.
+template <int TILE>
+__device__ __forceinline__ int2 pixel_of(int t) {
+  constexpr int BPR = TILE / 8;  // 8-wide blocks per tile row
+  const int w = t >> 5, lane = t & 31;
+  return make_int2((w % BPR) * 8 + (lane & 7), (w / BPR) * 4 + (lane >> 3));
+}
 
-// Top-K selection over the tile's list for pixel (px, py).
-template <int TILE, int K>
-__device__ __forceinline__ void select_topk(const RenderParams& p, int2 range, float px,
-                                            float py, float (&tq)[K], int (&tp)[K],
-                                            float4* s_a, float* s_a11) {
-  constexpr int NT = TILE * TILE;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    tq[k] = __int_as_float(0x7f800000);  // +inf
-    tp[k] = -1;
-  }
-  for (int base = range.x; base < range.y; base += NT) {
-    const int cnt = min(NT, range.y - base);
-    __syncthreads();
-    if ((int)threadIdx.x < cnt) {
-      const int gid = p.list[base + threadIdx.x];
-      if ((unsigned)gid < (unsigned)p.N) {
-        const GRec g = p.rec[gid];
-        s_a[threadIdx.x] = g.a;
-        s_a11[threadIdx.x] = g.b.x;
-      } else {  // corrupt list entry: a NaN key is never selected
-        s_a[threadIdx.x] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
-        s_a11[threadIdx.x] = 0.0f;
-        atomicOr(&p.status->flags, FLAG_INTERNAL);
-      }
-    }
-    __syncthreads();
-    const int rel = base - range.x;
-#pragma unroll 4
-    for (int j = 0; j < cnt; ++j) {
-      const float4 a = s_a[j];
-      const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_a11[j]);
-      if (__any_sync(FULL_MASK, q < tq[K - 1])) topk_insert<K>(tq, tp, q, rel + j);
+constexpr float F_INF = __builtin_huge_valf();
+
+// Stage list entries [base, base+cnt) of the tile: geometry and index.
+template <int NT>
+__device__ __forceinline__ void stage_chunk(const RenderParams& p, int base, int cnt,
+                                            float4* s_a, float* s_a11, int* s_gid) {
+  if ((int)threadIdx.x < cnt) {
+    const int gid = p.list[base + threadIdx.x];
+    if ((unsigned)gid < (unsigned)p.N) {
+      const GRec g = p.rec[gid];
+      s_a[threadIdx.x] = g.a;
+      s_a11[threadIdx.x] = g.b.x;
+      s_gid[threadIdx.x] = gid;
+    } else {  // corrupt list entry: a NaN key is never selected
+      s_a[threadIdx.x] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+      s_a11[threadIdx.x] = 0.0f;
+      s_gid[threadIdx.x] = -1;
+      atomicOr(&p.status->flags, FLAG_INTERNAL);
     }
   }
 }
 
-// Weights of the winners and the blended colour (Eq. 5, max-shifted).
-template <int K, int NC>
-__device__ __forceinline__ float blend(const RenderParams& p, int2 range, const float (&tq)[K],
-                                       const int (&tp)[K], float (&w)[K], int (&gid)[K],
-                                       float (&cr)[Chan<NC>::R]) {
-  const int n = nchan<NC>(p);
+// Pass A: the K smallest keys at (px, py), ascending.
+template <int TILE, int K>
+__device__ __forceinline__ void select_keys(const RenderParams& p, int2 range, float px,
+                                            float py, float (&tq)[K], float4* s_a, float* s_a11,
+                                            int* s_gid) {
+  constexpr int NT = TILE * TILE;
 #pragma unroll
-  for (int c = 0; c < Chan<NC>::R; ++c) cr[c] = 0.0f;
-  float Z = 0.0f;
+  for (int k = 0; k < K; ++k) tq[k] = F_INF;
+  for (int base = range.x; base < range.y; base += NT) {
+    const int cnt = min(NT, range.y - base);
+    __syncthreads();
+    stage_chunk<NT>(p, base, cnt, s_a, s_a11, s_gid);
+    __syncthreads();
+#pragma unroll 4
+    for (int j = 0; j < cnt; ++j) {
+      const float4 a = s_a[j];
+      const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_a11[j]);
+      const bool better = q < tq[K - 1];
+      if (__any_sync(FULL_MASK, better)) {
+        float x = better ? q : F_INF;  // +inf (and NaN) insert nothing
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    w[k] = 0.0f;
-    gid[k] = -1;
-    if (tp[k] >= 0) {
-      w[k] = exp2f((tq[0] - tq[k]) * HALF_LOG2E);
-      Z += w[k];
-      gid[k] = p.list[range.x + tp[k]];
-      const float* col = p.color + (int64_t)gid[k] * n;
-#pragma unroll
-      for (int c = 0; c < Chan<NC>::R; ++c)
-        if (NC > 0 || c < n) cr[c] = fmaf(w[k], col[c], cr[c]);
+        for (int k = 0; k < K; ++k) {
+          const float lo = fminf(tq[k], x);
+          x = fmaxf(tq[k], x);
+          tq[k] = lo;
+        }
+      }
     }
   }
-  const float iz = Z > 0.0f ? 1.0f / Z : 0.0f;
+}
+
+// Per-pixel result of pass B.
+template <int NCR>
+struct PixelBlend {
+  float Z;          // sum of winner weights (0 if the pixel has none)
+  float cr[NCR];    // blended colour
+  float tau;        // K-th key (+inf if |S_j| < K)
+  float q0;         // smallest key
+  int posK;         // list position of the last tau-valued winner
+};
+
+// Pass B: exact top-K membership in list order and the blend of Eq. 5.
+template <int TILE, int K, int NC>
+__device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, float px,
+                                           float py, const float (&tq)[K],
+                                           PixelBlend<Chan<NC>::R>& r, float4* s_a,
+                                           float* s_a11, int* s_gid) {
+  constexpr int NT = TILE * TILE;
+  constexpr int NCR = Chan<NC>::R;
+  const int n = nchan<NC>(p);
+  r.q0 = tq[0];
+  r.tau = tq[K - 1];
+  int lt = 0;
 #pragma unroll
-  for (int c = 0; c < Chan<NC>::R; ++c) cr[c] *= iz;
-  return iz;
+  for (int k = 0; k < K; ++k) lt += tq[k] < r.tau ? 1 : 0;
+  int eq_left = K - lt;  // tau-valued slots still open
+  r.posK = -1;
+  r.Z = 0.0f;
+#pragma unroll
+  for (int c = 0; c < NCR; ++c) r.cr[c] = 0.0f;
+  const float q0k = r.q0 * HALF_LOG2E;
+  for (int base = range.x; base < range.y; base += NT) {
+    const int cnt = min(NT, range.y - base);
+    __syncthreads();
+    stage_chunk<NT>(p, base, cnt, s_a, s_a11, s_gid);
+    __syncthreads();
+    const int rel = base - range.x;
+#pragma unroll 2
+    for (int j = 0; j < cnt; ++j) {
+      const float4 a = s_a[j];
+      const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_a11[j]);
+      bool win = q < r.tau;
+      if (q == r.tau && eq_left > 0) {
+        win = true;
+        --eq_left;
+        r.posK = rel + j;
+      }
+      if (__any_sync(FULL_MASK, win)) {
+        if (win) {
+          const float w = exp2f(fmaf(q, -HALF_LOG2E, q0k));
+          r.Z += w;
+          const float* col = p.color + (int64_t)s_gid[j] * n;
+#pragma unroll
+          for (int c = 0; c < NCR; ++c)
+            if (NC > 0 || c < n) r.cr[c] = fmaf(w, col[c], r.cr[c]);
+        }
+      }
+    }
+  }
+  const float iz = r.Z > 0.0f ? 1.0f / r.Z : 0.0f;
+#pragma unroll
+  for (int c = 0; c < NCR; ++c) r.cr[c] *= iz;
 }
 
 template <int TILE, int K, int NC>
@@ -106,124 +163,103 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(RenderParams p) {
   constexpr int NT = TILE * TILE;
   __shared__ float4 s_a[NT];
   __shared__ float s_a11[NT];
+  __shared__ int s_gid[NT];
   const int tile_id = blockIdx.x;
   const int tx = tile_id % p.tiles_x, ty = tile_id / p.tiles_x;
-  const int x = tx * TILE + (int)(threadIdx.x % TILE);
-  const int y = ty * TILE + (int)(threadIdx.x / TILE);
+  const int2 lp = pixel_of<TILE>(threadIdx.x);
+  const int x = tx * TILE + lp.x, y = ty * TILE + lp.y;
   const float px = (float)x + 0.5f, py = (float)y + 0.5f;
   const int2 range = p.range[tile_id];
   float tq[K];
-  int tp[K];
-  select_topk<TILE, K>(p, range, px, py, tq, tp, s_a, s_a11);
+  select_keys<TILE, K>(p, range, px, py, tq, s_a, s_a11, s_gid);
+  PixelBlend<Chan<NC>::R> r;
+  blend_pass<TILE, K, NC>(p, range, px, py, tq, r, s_a, s_a11, s_gid);
   if (x >= p.W || y >= p.H) return;
-  float w[K];
-  int gid[K];
-  float cr[Chan<NC>::R];
-  blend<K, NC>(p, range, tq, tp, w, gid, cr);
   const int n = nchan<NC>(p);
   const int64_t plane = (int64_t)p.H * p.W;
   const int64_t o = (int64_t)y * p.W + x;
 #pragma unroll
   for (int c = 0; c < Chan<NC>::R; ++c)
-    if (NC > 0 || c < n) p.img[c * plane + o] = cr[c];
+    if (NC > 0 || c < n) p.img[c * plane + o] = r.cr[c];
+}
+
+// Dynamic shared-memory layout of the adjoint kernel (floats).
+struct BwdSmem {
+  int a, a11, gid, ps0, ps1, gh, part, loss, total;
+};
+__host__ __device__ inline BwdSmem bwd_smem(int NT, int n) {
+  BwdSmem L;
+  int o = 0;
+  L.a = o;    o += 4 * NT;        // float4 staged geometry
+  L.a11 = o;  o += NT;
+  L.gid = o;  o += NT;
+  L.ps0 = o;  o += 4 * NT;        // float4 (px, py, tau, q0 * HALF_LOG2E)
+  L.ps1 = o;  o += 2 * NT;        // float2 (posK bits, beta)
+  L.gh = o;   o += n * NT;        // per-pixel -g/(2Z), channel-major
+  L.part = o; o += (5 + n) * NT;  // pass C partial sums
+  L.loss = o; o += 2 * (NT / 32); // doubles
+  L.total = o;
+  return L;
 }
 
 template <int TILE, int K, int NC>
 __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(RenderParams p) {
   constexpr int NT = TILE * TILE;
   constexpr int NCR = Chan<NC>::R;
-  constexpr int LCAP = AccCap<NC>::L;
-  __shared__ float4 s_a[NT];
-  __shared__ float s_a11[NT];
-  __shared__ float s_acc[LCAP * AccCap<NC>::NP];
-  __shared__ double s_loss[NT / 32];
+  extern __shared__ __align__(16) float smem[];
   const int n = nchan<NC>(p);
-  const int np = 5 + n;
+  const BwdSmem SL = bwd_smem(NT, n);
+  float4* s_a = reinterpret_cast<float4*>(smem + SL.a);
+  float* s_a11 = smem + SL.a11;
+  int* s_gid = reinterpret_cast<int*>(smem + SL.gid);
+  float4* s_ps0 = reinterpret_cast<float4*>(smem + SL.ps0);
+  float2* s_ps1 = reinterpret_cast<float2*>(smem + SL.ps1);
+  float* s_gh = smem + SL.gh;
+  float* s_part = smem + SL.part;
+  double* s_loss = reinterpret_cast<double*>(smem + SL.loss);
+
   const int tile_id = blockIdx.x;
   const int tx = tile_id % p.tiles_x, ty = tile_id / p.tiles_x;
-  const int x = tx * TILE + (int)(threadIdx.x % TILE);
-  const int y = ty * TILE + (int)(threadIdx.x / TILE);
+  const int2 lp = pixel_of<TILE>(threadIdx.x);
+  const int x = tx * TILE + lp.x, y = ty * TILE + lp.y;
   const float px = (float)x + 0.5f, py = (float)y + 0.5f;
   const int2 range = p.range[tile_id];
   const int len = range.y - range.x;
-  const int slots = min(len, LCAP);
-  for (int i = threadIdx.x; i < slots * np; i += NT) s_acc[i] = 0.0f;
 
+  // ---- passes A and B: per-pixel forward values and upstream gradient
   float tq[K];
-  int tp[K];
-  select_topk<TILE, K>(p, range, px, py, tq, tp, s_a, s_a11);
-  __syncthreads();  // s_acc zeroed before any contribution
+  select_keys<TILE, K>(p, range, px, py, tq, s_a, s_a11, s_gid);
+  PixelBlend<NCR> r;
+  blend_pass<TILE, K, NC>(p, range, px, py, tq, r, s_a, s_a11, s_gid);
 
   float loss = 0.0f;
-  const bool inside = x < p.W && y < p.H;
-  if (inside && len > 0) {
-    float w[K];
-    int gid[K];
-    float cr[NCR];
-    const float iz = blend<K, NC>(p, range, tq, tp, w, gid, cr);
-    const int64_t plane = (int64_t)p.H * p.W;
-    const int64_t o = (int64_t)y * p.W + x;
-    float g[NCR];
-    float gdot_r = 0.0f;
+  const bool live = x < p.W && y < p.H && r.Z > 0.0f;
+  float beta = 0.0f;
+  const float iz = live ? 1.0f / r.Z : 0.0f;
+  const int64_t plane = (int64_t)p.H * p.W;
+  const int64_t o = (int64_t)y * p.W + x;
 #pragma unroll
-    for (int c = 0; c < NCR; ++c) {
-      g[c] = 0.0f;
-      if (NC > 0 || c < n) {
+  for (int c = 0; c < NCR; ++c) {
+    if (NC > 0 || c < n) {
+      float g = 0.0f;
+      if (live) {
         if (p.grad_img) {
-          g[c] = p.grad_img[c * plane + o];
+          g = p.grad_img[c * plane + o];
         } else {
-          const float d = cr[c] - p.target[c * plane + o];
+          const float d = r.cr[c] - p.target[c * plane + o];
           loss += fabsf(d);
-          g[c] = sign_f(d) * p.inv_count;
+          g = sign_f(d) * p.inv_count;
         }
-        gdot_r = fmaf(g[c], cr[c], gdot_r);
       }
-    }
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      if (gid[k] < 0) continue;
-      const int id = gid[k];
-      const float wz = w[k] * iz;
-      const float* col = p.color + (int64_t)id * n;
-      float gdot = 0.0f;
-#pragma unroll
-      for (int c = 0; c < NCR; ++c)
-        if (NC > 0 || c < n) gdot = fmaf(g[c], col[c], gdot);
-      const float Gq = -0.5f * wz * (gdot - gdot_r);
-      const GRec rc = p.rec[id];
-      const float2 cs = p.trig[id];
-      const float dx = px - rc.a.x, dy = py - rc.a.y;
-      const float a = cs.x * dx + cs.y * dy;
-      const float b = -cs.y * dx + cs.x * dy;
-      const float t1 = rc.b.z, t2 = rc.b.w;
-      const float T1 = t1 * t1, T2 = t2 * t2;
-      const float Ta = T1 * a, Tb = T2 * b;
-      float v[5];
-      v[0] = Gq * -2.0f * (Ta * cs.x - Tb * cs.y) * (float)p.W;
-      v[1] = Gq * -2.0f * (Ta * cs.y + Tb * cs.x) * (float)p.H;
-      v[2] = Gq * 2.0f * a * b * (T1 - T2);
-      v[3] = Gq * 2.0f * t1 * a * a;
-      v[4] = Gq * 2.0f * t2 * b * b;
-      const int pos = tp[k];
-      if (pos < LCAP) {
-        float* dst = s_acc + pos * np;
-#pragma unroll
-        for (int j = 0; j < 5; ++j) atomicAdd(dst + j, v[j]);
-#pragma unroll
-        for (int c = 0; c < NCR; ++c)
-          if (NC > 0 || c < n) atomicAdd(dst + 5 + c, wz * g[c]);
-      } else {
-        float* dst = p.grad + (int64_t)id * np;
-#pragma unroll
-        for (int j = 0; j < 5; ++j) atomicAdd(dst + j, v[j]);
-#pragma unroll
-        for (int c = 0; c < NCR; ++c)
-          if (NC > 0 || c < n) atomicAdd(dst + 5 + c, wz * g[c]);
-      }
+      const float gh = -0.5f * g * iz;  // dL/dq_k = w_k * (sum_c gh_c c_k,c - beta)
+      beta = fmaf(gh, r.cr[c], beta);
+      s_gh[c * NT + threadIdx.x] = gh;
     }
   }
+  s_ps0[threadIdx.x] = make_float4(px, py, live ? r.tau : -F_INF, r.q0 * HALF_LOG2E);
+  s_ps1[threadIdx.x] = make_float2(__int_as_float(r.posK), beta);
   if (!p.grad_img) {
-    double l = warp_sum<double>((double)loss);
+    const double l = warp_sum<double>((double)loss);
     if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = l;
   }
   __syncthreads();
@@ -232,14 +268,101 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(RenderParams p) {
     for (int i = 0; i < NT / 32; ++i) t += s_loss[i];
     if (t != 0.0) atomicAdd(&p.status->loss_sum, t);
   }
-  for (int i = threadIdx.x; i < slots * np; i += NT) {
-    const float v = s_acc[i];
-    if (v != 0.0f) {
-      const int pos = i / np, j = i - pos * np;
-      const int id = p.list[range.x + pos];
-      atomicAdd(p.grad + (int64_t)id * np + j, v);
+
+  // ---- pass C: candidate-major accumulation of the adjoint
+  const int np = 5 + n;
+  for (int cbase = range.x; cbase < range.y; cbase += NT) {
+    const int C = min(NT, range.y - cbase);
+    const int G = max(1, NT / C);            // pixel groups per candidate
+    const int PPG = (NT + G - 1) / G;        // pixels per group
+    const int j = (int)threadIdx.x % C;
+    const int grp = (int)threadIdx.x / C;
+    float S1 = 0.f, S2 = 0.f, S11 = 0.f, S12 = 0.f, S22 = 0.f;
+    float Sc[NCR];
+#pragma unroll
+    for (int c = 0; c < NCR; ++c) Sc[c] = 0.0f;
+    const int gid = p.list[cbase + j];
+    const bool act = grp < G && (unsigned)gid < (unsigned)p.N;
+    if (act) {
+      const int pos = cbase - range.x + j;
+      const GRec rc = p.rec[gid];
+      const float* col = p.color + (int64_t)gid * n;
+      float cc[NCR];
+#pragma unroll
+      for (int c = 0; c < NCR; ++c) cc[c] = (NC > 0 || c < n) ? col[c] : 0.0f;
+      const int i0 = grp * PPG, i1 = min(NT, i0 + PPG);
+      for (int i = i0; i < i1; ++i) {
+        const float4 s0 = s_ps0[i];
+        const float2 s1 = s_ps1[i];
+        const float dx = __fsub_rn(s0.x, rc.a.x);
+        const float dy = __fsub_rn(s0.y, rc.a.y);
+        const float h = __fmaf_rn(rc.a.w, dy, __fmul_rn(rc.a.z, dx));
+        const float q = __fmaf_rn(h, dx, __fmul_rn(__fmul_rn(rc.b.x, dy), dy));
+        const bool win = q < s0.z || (q == s0.z && pos <= __float_as_int(s1.x));
+        if (win) {
+          const float w = exp2f(fmaf(q, -HALF_LOG2E, s0.w));
+          float gd = -s1.y;
+#pragma unroll
+          for (int c = 0; c < NCR; ++c)
+            if (NC > 0 || c < n) gd = fmaf(s_gh[c * NT + i], cc[c], gd);
+          const float Gq = w * gd;
+          const float e1 = Gq * dx, e2 = Gq * dy;
+          S1 += e1;
+          S2 += e2;
+          S11 = fmaf(e1, dx, S11);
+          S12 = fmaf(e1, dy, S12);
+          S22 = fmaf(e2, dy, S22);
+#pragma unroll
+          for (int c = 0; c < NCR; ++c)
+            if (NC > 0 || c < n) Sc[c] = fmaf(w, s_gh[c * NT + i], Sc[c]);
+        }
+      }
     }
+    if (grp < G) {
+      float* dst = s_part + (grp * C + j) * np;
+      dst[0] = S1;
+      dst[1] = S2;
+      dst[2] = S11;
+      dst[3] = S12;
+      dst[4] = S22;
+#pragma unroll
+      for (int c = 0; c < NCR; ++c)
+        if (NC > 0 || c < n) dst[5 + c] = Sc[c];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < C && (unsigned)gid < (unsigned)p.N) {
+      float T[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      for (int g2 = 0; g2 < G; ++g2) {
+        const float* src = s_part + (g2 * C + j) * np;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) T[k] += src[k];
+      }
+      const GRec rc = p.rec[gid];
+      const float2 cs = p.trig[gid];
+      const float A00 = rc.a.z, B = rc.a.w, A11 = rc.b.x, t1 = rc.b.z, t2 = rc.b.w;
+      const float T1 = t1 * t1, T2 = t2 * t2;
+      const float c2 = cs.x * cs.x, s2 = cs.y * cs.y, sc = cs.x * cs.y;
+      // q = A00 dx^2 + B dx dy + A11 dy^2, d = x - mu_px
+      const float d_mx = -(2.0f * A00 * T[0] + B * T[1]);
+      const float d_my = -(B * T[0] + 2.0f * A11 * T[1]);
+      const float dT1 = T[2] * c2 + T[4] * s2 + 2.0f * T[3] * sc;
+      const float dT2 = T[2] * s2 + T[4] * c2 - 2.0f * T[3] * sc;
+      const float d_th = (T1 - T2) * (2.0f * sc * (T[4] - T[2]) + 2.0f * (c2 - s2) * T[3]);
+      float* gdst = p.grad + (int64_t)gid * np;
+      atomicAdd(gdst + 0, d_mx * (float)p.W);
+      atomicAdd(gdst + 1, d_my * (float)p.H);
+      atomicAdd(gdst + 2, d_th);
+      atomicAdd(gdst + 3, 2.0f * t1 * dT1);
+      atomicAdd(gdst + 4, 2.0f * t2 * dT2);
+      for (int c = 0; c < n; ++c) {
+        float sc_ = 0.0f;
+        for (int g2 = 0; g2 < G; ++g2) sc_ += s_part[(g2 * C + j) * np + 5 + c];
+        atomicAdd(gdst + 5 + c, -2.0f * sc_);  // w g / Z = w * (-2 gh)
+      }
+    }
+    __syncthreads();
   }
+  (void)len;
 }
 
 // One thread per query point: its tile's list is walked from global memory.
@@ -256,7 +379,7 @@ __global__ void __launch_bounds__(256) k_decode(RenderParams p) {
   int tp[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    tq[k] = __int_as_float(0x7f800000);
+    tq[k] = F_INF;
     tp[k] = -1;
   }
   for (int j = range.x; j < range.y; ++j) {
@@ -264,16 +387,29 @@ __global__ void __launch_bounds__(256) k_decode(RenderParams p) {
     if ((unsigned)id >= (unsigned)p.N) continue;
     const GRec g = p.rec[id];
     const float q = rank_key(px, py, g.a.x, g.a.y, g.a.z, g.a.w, g.b.x);
-    if (q < tq[K - 1]) topk_insert<K>(tq, tp, q, j - range.x);
+    if (q < tq[K - 1]) topk_insert<K>(tq, tp, q, id);
   }
-  float w[K];
-  int gid[K];
-  float cr[Chan<NC>::R];
-  blend<K, NC>(p, range, tq, tp, w, gid, cr);
   const int n = nchan<NC>(p);
+  constexpr int NCR = Chan<NC>::R;
+  float cr[NCR];
 #pragma unroll
-  for (int c = 0; c < Chan<NC>::R; ++c)
-    if (NC > 0 || c < n) p.qout[qi * n + c] = cr[c];
+  for (int c = 0; c < NCR; ++c) cr[c] = 0.0f;
+  float Z = 0.0f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (tp[k] >= 0) {
+      const float w = exp2f(fmaf(tq[k], -HALF_LOG2E, tq[0] * HALF_LOG2E));
+      Z += w;
+      const float* col = p.color + (int64_t)tp[k] * n;
+#pragma unroll
+      for (int c = 0; c < NCR; ++c)
+        if (NC > 0 || c < n) cr[c] = fmaf(w, col[c], cr[c]);
+    }
+  }
+  const float iz = Z > 0.0f ? 1.0f / Z : 0.0f;
+#pragma unroll
+  for (int c = 0; c < NCR; ++c)
+    if (NC > 0 || c < n) p.qout[qi * n + c] = cr[c] * iz;
 }
 
 // Dispatch over the supported K and channel counts.

@@ -3,38 +3,54 @@
 
 namespace igs {
 
-#define IGS_FWD_NC(KK, nc)                                                                 \
-  switch (nc) {                                                                            \
-    case 1: k_render_fwd<8, KK, 1><<<grid, 8 * 8, 0, s>>>(p); break;                    \
-    case 3: k_render_fwd<8, KK, 3><<<grid, 8 * 8, 0, s>>>(p); break;                    \
-    case 4: k_render_fwd<8, KK, 4><<<grid, 8 * 8, 0, s>>>(p); break;                    \
-    case 9: k_render_fwd<8, KK, 9><<<grid, 8 * 8, 0, s>>>(p); break;                    \
-    default: k_render_fwd<8, KK, 0><<<grid, 8 * 8, 0, s>>>(p); break;                   \
-  }
+namespace {
 
-#define IGS_BWD_NC(KK, nc)                                                                 \
-  switch (nc) {                                                                            \
-    case 1: k_render_bwd<8, KK, 1><<<grid, 8 * 8, 0, s>>>(p); break;                    \
-    case 3: k_render_bwd<8, KK, 3><<<grid, 8 * 8, 0, s>>>(p); break;                    \
-    case 4: k_render_bwd<8, KK, 4><<<grid, 8 * 8, 0, s>>>(p); break;                    \
-    case 9: k_render_bwd<8, KK, 9><<<grid, 8 * 8, 0, s>>>(p); break;                    \
-    default: k_render_bwd<8, KK, 0><<<grid, 8 * 8, 0, s>>>(p); break;                   \
+template <int KK, int NCC>
+cudaError_t fwd_inst(const RenderParams& p, unsigned grid, cudaStream_t s) {
+  k_render_fwd<8, KK, NCC><<<grid, 8 * 8, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int KK, int NCC>
+cudaError_t bwd_inst(const RenderParams& p, unsigned grid, cudaStream_t s) {
+  const size_t bytes = sizeof(float) * (size_t)bwd_smem(8 * 8, NCC > 0 ? NCC : p.n).total;
+  if (bytes > 48 * 1024) {
+    static bool raised = false;  // idempotent; a repeated call is harmless
+    if (!raised) {
+      cudaError_t e = cudaFuncSetAttribute(k_render_bwd<8, KK, NCC>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)bytes);
+      if (e != cudaSuccess) return e;
+      raised = true;
+    }
+  }
+  k_render_bwd<8, KK, NCC><<<grid, 8 * 8, bytes, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#define IGS_NC_SWITCH(KK, FN)                                  \
+  switch (IGS_NC_OF(p.n)) {                                    \
+    case 1: return FN<KK, 1>(p, grid, s);                      \
+    case 3: return FN<KK, 3>(p, grid, s);                      \
+    case 4: return FN<KK, 4>(p, grid, s);                      \
+    case 9: return FN<KK, 9>(p, grid, s);                      \
+    default: return FN<KK, 0>(p, grid, s);                     \
   }
 
 cudaError_t launch_render_fwd_t8(const RenderParams& p, int K, cudaStream_t s) {
   const unsigned grid = (unsigned)(p.tiles_x * p.tiles_y);
   if (grid == 0) return cudaSuccess;
-  const int nc = IGS_NC_OF(p.n);
-  IGS_FOR_K(IGS_FWD_NC, nc)
-  return cudaGetLastError();
+  IGS_FOR_K(IGS_NC_SWITCH, fwd_inst)
+  return cudaSuccess;
 }
 
 cudaError_t launch_render_bwd_t8(const RenderParams& p, int K, cudaStream_t s) {
   const unsigned grid = (unsigned)(p.tiles_x * p.tiles_y);
   if (grid == 0) return cudaSuccess;
-  const int nc = IGS_NC_OF(p.n);
-  IGS_FOR_K(IGS_BWD_NC, nc)
-  return cudaGetLastError();
+  IGS_FOR_K(IGS_NC_SWITCH, bwd_inst)
+  return cudaSuccess;
 }
 
 }  // namespace igs
