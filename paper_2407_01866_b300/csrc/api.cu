@@ -104,8 +104,8 @@ static int check_gaussians(const igs_gaussians* g) {
     return fail(IGS_ERR_INVALID_ARG, "dtype %d unknown", g->dtype);
   if (g->N > 0 && (!g->xy || !g->theta || !g->inv_scale || !g->color))
     return fail(IGS_ERR_INVALID_ARG, "a parameter array is NULL");
-  if (g->xy_stride < 2 || g->theta_stride < 1 || g->inv_scale_stride < 2 ||
-      g->color_stride < g->n)
+  if (g->N > 0 && (g->xy_stride < 2 || g->theta_stride < 1 || g->inv_scale_stride < 2 ||
+                   g->color_stride < g->n))
     return fail(IGS_ERR_INVALID_ARG, "parameter row strides too small");
   const size_t es = g->dtype == IGS_F32 ? 4 : 2;
   if (!aligned(g->xy, es) || !aligned(g->theta, es) || !aligned(g->inv_scale, es) ||

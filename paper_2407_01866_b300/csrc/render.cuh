@@ -124,7 +124,6 @@ __device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, fl
   r.Z = 0.0f;
 #pragma unroll
   for (int c = 0; c < NCR; ++c) r.cr[c] = 0.0f;
-  const float q0k = r.q0 * HALF_LOG2E;
   for (int base = range.x; base < range.y; base += NT) {
     const int cnt = min(NT, range.y - base);
     __syncthreads();
@@ -143,7 +142,7 @@ __device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, fl
       }
       if (__any_sync(FULL_MASK, win)) {
         if (win) {
-          const float w = exp2f(fmaf(q, -HALF_LOG2E, q0k));
+          const float w = exp2f((r.q0 - q) * HALF_LOG2E);  // exactly 1 at q = q_min
           r.Z += w;
           const float* col = p.color + (int64_t)s_gid[j] * n;
 #pragma unroll
@@ -193,7 +192,7 @@ __host__ __device__ inline BwdSmem bwd_smem(int NT, int n) {
   L.a = o;    o += 4 * NT;        // float4 staged geometry
   L.a11 = o;  o += NT;
   L.gid = o;  o += NT;
-  L.ps0 = o;  o += 4 * NT;        // float4 (px, py, tau, q0 * HALF_LOG2E)
+  L.ps0 = o;  o += 4 * NT;        // float4 (px, py, tau, q0)
   L.ps1 = o;  o += 2 * NT;        // float2 (posK bits, beta)
   L.gh = o;   o += n * NT;        // per-pixel -g/(2Z), channel-major
   L.part = o; o += (5 + n) * NT;  // pass C partial sums
@@ -256,7 +255,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(RenderParams p) {
       s_gh[c * NT + threadIdx.x] = gh;
     }
   }
-  s_ps0[threadIdx.x] = make_float4(px, py, live ? r.tau : -F_INF, r.q0 * HALF_LOG2E);
+  s_ps0[threadIdx.x] = make_float4(px, py, live ? r.tau : -F_INF, r.q0);
   s_ps1[threadIdx.x] = make_float2(__int_as_float(r.posK), beta);
   if (!p.grad_img) {
     const double l = warp_sum<double>((double)loss);
@@ -300,7 +299,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(RenderParams p) {
         const float q = __fmaf_rn(h, dx, __fmul_rn(__fmul_rn(rc.b.x, dy), dy));
         const bool win = q < s0.z || (q == s0.z && pos <= __float_as_int(s1.x));
         if (win) {
-          const float w = exp2f(fmaf(q, -HALF_LOG2E, s0.w));
+          const float w = exp2f((s0.w - q) * HALF_LOG2E);
           float gd = -s1.y;
 #pragma unroll
           for (int c = 0; c < NCR; ++c)
@@ -398,7 +397,7 @@ __global__ void __launch_bounds__(256) k_decode(RenderParams p) {
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     if (tp[k] >= 0) {
-      const float w = exp2f(fmaf(tq[k], -HALF_LOG2E, tq[0] * HALF_LOG2E));
+      const float w = exp2f((tq[0] - tq[k]) * HALF_LOG2E);
       Z += w;
       const float* col = p.color + (int64_t)tp[k] * n;
 #pragma unroll

@@ -154,7 +154,7 @@ def gaussians_view(xy, theta, inv_scale, color):
             raise ValueError("all parameter tensors must share one dtype")
     N = xy.shape[0]
     n = color.shape[1]
-    if xy.stride(1) != 1 or inv_scale.stride(1) != 1 or color.stride(1) != 1:
+    if N > 0 and (xy.stride(1) != 1 or inv_scale.stride(1) != 1 or color.stride(1) != 1):
         raise ValueError("parameter rows must be contiguous")
     g = Gaussians(xy.data_ptr(), theta.data_ptr(), inv_scale.data_ptr(), color.data_ptr(),
                   xy.stride(0), theta.stride(0), inv_scale.stride(0), color.stride(0), N, n, dt)
