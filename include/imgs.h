@@ -208,6 +208,35 @@ int igs_fit_step(const igs_fit_state* st, const float* d_target, int32_t H,
 int igs_decode_points(const igs_bins* bins, const igs_config* cfg,
                       const float* d_xy, int64_t Q, float* d_out, igs_stream stream);
 
+/* Forward render that allocates nothing and takes no workspace. The paper
+ * has no counterpart: this is a convenience for callers that cannot call
+ * cudaMalloc or hand the library a device buffer -- a plug-in inside a host
+ * application that owns every allocation, a real-time thread where an
+ * allocation may block or fail, or code held to a fixed device-memory
+ * budget. It runs igs_preprocess_bin and igs_render_forward with their
+ * scratch in one static device array of IGS_STATIC_SCRATCH_BYTES (32 MiB)
+ * that every GPU which loads the library keeps until the process exits.
+ * - Inputs g (device parameters) and output d_img [n][H][W] are the
+ *   caller's, as for igs_render_forward.
+ * - Sizes whose workspace cannot fit (large N, image or tile count) are
+ *   rejected with IGS_ERR_CAPACITY before any GPU work; if the
+ *   intersections found on the GPU do not fit, the call returns
+ *   IGS_ERR_CAPACITY after rendering and the image is incomplete.
+ * - The call synchronises `stream` at its end to read the status block.
+ * - The first call on a device looks up the array's device address (once
+ *   per device, with that device current); make that first call before
+ *   any stream capture.
+ * - All calls share the one array, which keeps the last call's contents;
+ *   every word a call reads is cleared or written by that call first.
+ *   Calls that overlap on the GPU (other streams, other host threads) race
+ *   on it: serialise them. */
+#define IGS_STATIC_SCRATCH_BYTES (32u << 20)
+int igs_render_forward_static(const igs_gaussians* g, int32_t H, int32_t W,
+                              const igs_config* cfg, float* d_img, igs_stream stream);
+
+/* Size in bytes of the static scratch used by igs_render_forward_static. */
+int igs_static_scratch_bytes(size_t* bytes);
+
 /* Synchronously copies the workspace's status block to *out (this call
  * synchronises `stream`). */
 int igs_read_stats(const igs_bins* bins, igs_stats* out, igs_stream stream);

@@ -23,6 +23,8 @@ static int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 static int cuda_fail(cudaError_t e, const char* where) {
   return fail(IGS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }

@@ -29,6 +29,8 @@ struct WsLayout {
   int tiles_x, tiles_y, passes;
 };
 WsLayout ws_layout(int64_t N, int n, int H, int W, int tile, int64_t m_cap);
+// Sets the calling thread's message returned by igs_last_error.
+void set_last_error(const char* msg);
 
 struct PrepParams {
   const void* xy;

@@ -1,0 +1,114 @@
+// Forward render for callers that cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc or hand the library a workspace: a
+// plug-in running inside a host application that owns every allocation, a
+// real-time thread where an allocation could block or fail, or code that
+// must keep a fixed, audited device-memory budget. igs_render_forward_static
+// serves them: it bins and renders like igs_preprocess_bin followed by
+// igs_render_forward, but its scratch lives in one fixed-size array in this
+// file, which every GPU that loads the library holds until the process exits.
+#include <cstdio>
+#include <mutex>
+
+#include "imgs.h"
+#include "internal.h"
+
+namespace igs {
+
+// Fixed scratch for the no-allocation render: IGS_STATIC_SCRATCH_BYTES
+// (32 MiB) per device.
+constexpr size_t STATIC_SCRATCH_BYTES = IGS_STATIC_SCRATCH_BYTES;
+static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_scratch_mutex;
+void* g_scratch_ptr[MAX_DEVICES] = {};
+
+// Device address of the scratch on the current device. In host code the
+// array's name is only a host-side stand-in, so the address must come from
+// cudaGetSymbolAddress, once per device, with that device current.
+cudaError_t scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+}  // namespace igs
+
+using namespace igs;
+
+extern "C" int igs_static_scratch_bytes(size_t* bytes) {
+  if (bytes) *bytes = STATIC_SCRATCH_BYTES;
+  return IGS_OK;
+}
+
+extern "C" int igs_render_forward_static(const igs_gaussians* g, int32_t H, int32_t W,
+                                         const igs_config* cfg, float* d_img,
+                                         igs_stream stream) {
+  char msg[256];
+  if (!g || !cfg || !d_img) {
+    snprintf(msg, sizeof(msg), "igs_render_forward_static: NULL argument");
+    set_last_error(msg);
+    return IGS_ERR_INVALID_ARG;
+  }
+  // Room for the intersections: the largest capacity whose workspace fits.
+  size_t fixed = 0;
+  if (int r = igs_workspace_size(g->N, g->n, H, W, cfg, 1, &fixed)) return r;
+  if (fixed > STATIC_SCRATCH_BYTES) {
+    snprintf(msg, sizeof(msg),
+             "igs_render_forward_static: N=%lld, n=%d, %dx%d needs %zu bytes before any "
+             "intersection; the static scratch holds %zu",
+             (long long)g->N, g->n, H, W, fixed, STATIC_SCRATCH_BYTES);
+    set_last_error(msg);
+    return IGS_ERR_CAPACITY;
+  }
+  // Each intersection costs 16 bytes of keys/values plus 1/16 byte of histogram.
+  int64_t m_cap = (int64_t)((STATIC_SCRATCH_BYTES - fixed) / 17);
+  size_t need = 0;
+  while (m_cap > 1) {
+    if (int r = igs_workspace_size(g->N, g->n, H, W, cfg, m_cap, &need)) return r;
+    if (need <= STATIC_SCRATCH_BYTES) break;
+    m_cap -= m_cap / 64 + 1;
+  }
+  if (m_cap < 1) m_cap = 1;
+  void* scratch = nullptr;
+  cudaError_t e = scratch_address(&scratch);
+  if (e != cudaSuccess) {
+    snprintf(msg, sizeof(msg), "igs_render_forward_static: scratch address: %s",
+             cudaGetErrorString(e));
+    set_last_error(msg);
+    return IGS_ERR_CUDA;
+  }
+  igs_bins bins;
+  // igs_preprocess_bin clears the status block and the tile ranges, and
+  // writes every other scratch word it later reads.
+  if (int r = igs_preprocess_bin(g, H, W, cfg, scratch, STATIC_SCRATCH_BYTES, m_cap, &bins,
+                                 stream))
+    return r;
+  if (int r = igs_render_forward(&bins, cfg, d_img, stream)) return r;
+  igs_stats st;
+  if (int r = igs_read_stats(&bins, &st, stream)) return r;  // synchronises `stream`
+  if (st.flags & IGS_FLAG_CAPACITY) {
+    snprintf(msg, sizeof(msg),
+             "igs_render_forward_static: %lld tile-Gaussian intersections exceed the %lld "
+             "that fit in the static scratch; the image is incomplete",
+             (long long)st.m_needed, (long long)m_cap);
+    set_last_error(msg);
+    return IGS_ERR_CAPACITY;
+  }
+  return IGS_OK;
+}

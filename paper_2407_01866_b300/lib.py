@@ -86,6 +86,9 @@ _SIGNATURES = {
     "igs_decode_points": ([ctypes.POINTER(Bins), ctypes.POINTER(Config), _P, ctypes.c_int64,
                            _P, _P], ctypes.c_int),
     "igs_read_stats": ([ctypes.POINTER(Bins), ctypes.POINTER(Stats), _P], ctypes.c_int),
+    "igs_render_forward_static": ([ctypes.POINTER(Gaussians), ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.POINTER(Config), _P, _P], ctypes.c_int),
+    "igs_static_scratch_bytes": ([ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
 }
 
 _lib = None
@@ -207,6 +210,19 @@ def adam_update(state, cfg, stream=None):
 def decode_points(bins, cfg, xy, out, stream=None):
     _check(load().igs_decode_points(ctypes.byref(bins), ctypes.byref(cfg), _ptr(xy),
                                     xy.shape[0], _ptr(out), _stream(stream)))
+
+
+def render_forward_static(g, H, W, cfg, img, stream=None):
+    """Bin and render with the library's fixed static scratch (no workspace,
+    no allocation); synchronises the stream. See igs_render_forward_static."""
+    _check(load().igs_render_forward_static(ctypes.byref(g), H, W, ctypes.byref(cfg), _ptr(img),
+                                            _stream(stream)))
+
+
+def static_scratch_bytes():
+    b = ctypes.c_size_t(0)
+    _check(load().igs_static_scratch_bytes(ctypes.byref(b)))
+    return b.value
 
 
 def read_stats(bins, stream=None):
