@@ -198,6 +198,15 @@ def run_ours(args):
         L.fit_step(state, target, H, W, cfg, ws, cap, loss)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
 
+    if args.kernel_once:
+        # one binning, one forward and one fused adjoint launch (for ncu captures)
+        bins = L.preprocess_bin(L.packed_view(P, n), H, W, cfg, ws, cap)
+        img = torch.empty((n, H, W), device=dev)
+        L.render_forward(bins, cfg, img)
+        L.render_backward(L.packed_view(P, n), bins, cfg, None, target, G)
+        torch.cuda.synchronize()
+        return
+
     for _ in range(args.warmup):
         graph.replay()
     torch.cuda.synchronize()
@@ -302,6 +311,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--kernel-once", action="store_true",
+                    help="bin, render and run the fused adjoint once, then exit (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

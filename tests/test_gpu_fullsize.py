@@ -1,0 +1,114 @@
+"""Parity at the full workload sizes, on outputs the oracle computes one by one.
+
+* forward: 2048 random pixels plus every pixel of 4 random tiles;
+* adjoint: an upstream gradient that is zero except at the sampled pixels, so
+  the oracle's gradient over those pixels alone is the exact reference;
+* fused L1 adjoint: equals the adjoint of the upstream gradient
+  sign(c_r - c_t)/(HWn) built from the kernel's own image (holds at any size);
+* half-precision storage at 8192^2: forward pixels and random-point decode.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import image_gs as O  # noqa: E402
+from paper_2407_01866_b300 import lib as L  # noqa: E402
+from paper_2407_01866_b300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from gpu_harness import grad_rel_error  # noqa: E402
+
+PIX_TOL = 1e-5
+HALF_TOL = 2e-3
+GRAD_TOL = 1e-3
+
+
+def sample_set(H, W, n_pix, n_tiles, seed, tile=16):
+    pix = synth.sample_pixels(n_pix, H, W, seed)
+    rng = np.random.default_rng(seed + 7)
+    tiles = []
+    for _ in range(n_tiles):
+        tx, ty = rng.integers(0, W // tile), rng.integers(0, H // tile)
+        hh, ww = np.meshgrid(np.arange(ty * tile, ty * tile + tile),
+                             np.arange(tx * tile, tx * tile + tile), indexing="ij")
+        tiles.append(np.stack([hh.ravel(), ww.ravel()], 1))
+    allp = np.concatenate([pix] + tiles)
+    return np.unique(allp, axis=0)
+
+
+def run_config(name, seed, dtype=torch.float32, n_pix=2048, n_tiles=4):
+    c = synth.CONFIGS[name]
+    H, W, n, N = c["H"], c["W"], c["n"], c["N"]
+    d = synth.gaussians(N, n, seed)
+    if dtype != torch.float32:
+        d = {k: torch.from_numpy(v).to(dtype).float().numpy() for k, v in d.items()}
+    g = O.Gaussians(d["xy"], d["theta"], d["inv_scale"], d["color"])
+    ts = [torch.from_numpy(d[k]).cuda().to(dtype) for k in ("xy", "theta", "inv_scale", "color")]
+    view = L.gaussians_view(*ts)
+    cfg = L.default_config()
+    binner = L.Binner(N, n, H, W, cfg)
+    bins = binner.bin(view)
+    assert L.read_stats(bins).flags == 0
+    img = torch.empty((n, H, W), device="cuda")
+    L.render_forward(bins, cfg, img)
+    pix = sample_set(H, W, n_pix, n_tiles, seed)
+    got = img[:, pix[:, 0], pix[:, 1]].T.cpu().numpy()
+    return dict(H=H, W=W, n=n, N=N, g=g, ts=ts, view=view, cfg=cfg, bins=bins, img=img,
+                pix=pix, got=got)
+
+
+@pytest.mark.parametrize("name", ["fit2048_rgb", "fit4096_tex9"])
+def test_fullsize_forward_and_adjoint_on_sampled_pixels(name):
+    r = run_config(name, seed=0, n_pix=1024 if name == "fit4096_tex9" else 2048)
+    want = O.render_pixels(r["g"], r["pix"], r["H"], r["W"])
+    assert np.abs(r["got"] - want).max() <= PIX_TOL
+    # sparse upstream gradient at the sampled pixels only
+    rng = np.random.default_rng(3)
+    vals = rng.standard_normal((len(r["pix"]), r["n"])).astype(np.float32)
+    gimg = torch.zeros((r["n"], r["H"], r["W"]), device="cuda")
+    pt = torch.from_numpy(r["pix"]).cuda()
+    gimg[:, pt[:, 0], pt[:, 1]] = torch.from_numpy(vals.T.copy()).cuda()
+    grad = torch.empty((r["N"], 5 + r["n"]), device="cuda")
+    L.render_backward(r["view"], r["bins"], r["cfg"], gimg, None, grad)
+    ref = O.backward_pixels(r["g"], r["pix"], vals.astype(np.float64), r["H"], r["W"])
+    errs = grad_rel_error(grad.cpu().numpy().astype(np.float64), ref)
+    assert max(errs.values()) <= GRAD_TOL, errs
+
+
+def test_fullsize_fused_l1_equals_adjoint_of_its_own_sign_gradient():
+    r = run_config("fit2048_rgb", seed=1, n_pix=16, n_tiles=0)
+    c = synth.CONFIGS["fit2048_rgb"]
+    target = torch.from_numpy(synth.target_image(r["H"], r["W"], 3, seed=1, n_sin=c["n_sin"],
+                                                 n_rect=c["n_rect"], noise_octaves=c["noise"])).cuda()
+    g_fused = torch.empty((r["N"], 8), device="cuda")
+    L.render_backward(r["view"], r["bins"], r["cfg"], None, target, g_fused)
+    st = L.read_stats(r["bins"])
+    inv = 1.0 / (r["H"] * r["W"] * 3)
+    gimg = torch.sign(r["img"] - target) * inv
+    g_ext = torch.empty_like(g_fused)
+    L.render_backward(r["view"], r["bins"], r["cfg"], gimg, None, g_ext)
+    errs = grad_rel_error(g_fused.cpu().numpy().astype(np.float64),
+                          g_ext.cpu().numpy().astype(np.float64))
+    assert max(errs.values()) <= 1e-5, errs
+    loss = (r["img"] - target).abs().double().mean().item()
+    assert abs(st.loss_sum * inv - loss) <= 1e-6 * max(1.0, loss)
+
+
+@pytest.mark.parametrize("dt", [torch.float16, torch.bfloat16])
+def test_decode8192_half_storage_pixels_and_points(dt):
+    r = run_config("decode8192_rgb", seed=0, dtype=dt, n_pix=512, n_tiles=2)
+    want = O.render_pixels(r["g"], r["pix"], r["H"], r["W"])
+    err = np.abs(r["got"] - want).max()
+    assert err <= HALF_TOL and err <= PIX_TOL, err
+    pts = synth.query_points(1_000_000, r["H"], r["W"], seed=0)
+    q = torch.from_numpy(pts).cuda()
+    out = torch.empty((len(pts), 3), device="cuda")
+    L.decode_points(r["bins"], r["cfg"], q, out)
+    sel = np.random.default_rng(5).choice(len(pts), 512, replace=False)
+    want = O.render_points(r["g"], pts[sel].astype(np.float64), r["H"], r["W"])
+    assert np.abs(out.cpu().numpy()[sel] - want).max() <= PIX_TOL
