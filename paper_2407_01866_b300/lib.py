@@ -185,6 +185,7 @@ def preprocess_bin(g, H, W, cfg, ws, m_capacity, stream=None):
     bins = Bins()
     _check(load().igs_preprocess_bin(ctypes.byref(g), H, W, ctypes.byref(cfg), _ptr(ws),
                                      ws.numel(), m_capacity, ctypes.byref(bins), _stream(stream)))
+    bins._workspace = ws   # the bins point into ws: keep it alive with them
     return bins
 
 

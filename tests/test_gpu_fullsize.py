@@ -58,8 +58,8 @@ def run_config(name, seed, dtype=torch.float32, n_pix=2048, n_tiles=4):
     L.render_forward(bins, cfg, img)
     pix = sample_set(H, W, n_pix, n_tiles, seed)
     got = img[:, pix[:, 0], pix[:, 1]].T.cpu().numpy()
-    return dict(H=H, W=W, n=n, N=N, g=g, ts=ts, view=view, cfg=cfg, bins=bins, img=img,
-                pix=pix, got=got)
+    return dict(H=H, W=W, n=n, N=N, g=g, ts=ts, view=view, cfg=cfg, binner=binner, bins=bins,
+                img=img, pix=pix, got=got)
 
 
 @pytest.mark.parametrize("name", ["fit2048_rgb", "fit4096_tex9"])
