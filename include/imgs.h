@@ -208,6 +208,59 @@ int igs_fit_step(const igs_fit_state* st, const float* d_target, int32_t H,
 int igs_decode_points(const igs_bins* bins, const igs_config* cfg,
                       const float* d_xy, int64_t Q, float* d_out, igs_stream stream);
 
+/* ---- Batched form: many images of uneven size fitted in one launch ----
+ * B images with their own H_b x W_b and N_b Gaussians share one fit state:
+ * parameters (and gradients, Adam moments) are the images' packed rows
+ * concatenated in image order, [sum N_b][5+n]; targets are the images'
+ * planar [n][H_b][W_b] float32 arrays concatenated in image order. Tiles
+ * are 16x16 and every image keeps its own tile grid (S_j per image). */
+typedef struct {
+  int32_t B;          /* number of images, >= 1 */
+  int32_t n;          /* channels, shared by all images */
+  const int32_t* H;   /* [B] host array: image heights */
+  const int32_t* W;   /* [B] host array: image widths */
+  const int64_t* N;   /* [B] host array: Gaussians per image */
+} igs_batch_shape;
+
+/* Physical mapping of the persistent adjoint (chosen by igs_autotune_batch). */
+typedef struct {
+  int32_t ctas_per_sm;  /* persistent CTAs per SM, 1..8 (default 4) */
+  int32_t stage;        /* Gaussians staged per round: 64, 128 or 256 (default 256) */
+  int32_t order;        /* 0: tiles pulled from a device counter, 1: static round-robin */
+} igs_batch_tuning;
+
+/* Workspace bytes for a batch (host only). m_capacity bounds the total
+ * tile-Gaussian intersections of all images. */
+int igs_batch_workspace_size(const igs_batch_shape* shape, const igs_config* cfg,
+                             int64_t m_capacity, size_t* bytes);
+
+/* Writes the batch's per-image tables (sizes, tile and pixel offsets, the
+ * image of every Gaussian) into the workspace. Call once per workspace and
+ * shape, before capturing igs_fit_batch_step: it copies from host memory. */
+int igs_batch_setup(const igs_batch_shape* shape, const igs_config* cfg, void* ws,
+                    size_t ws_bytes, int64_t m_capacity, igs_stream stream);
+
+/* One optimisation step of every image of the batch (Sec. 3.3, Sec. 4.1,
+ * as igs_fit_step): batched preprocess/bin over the concatenated tile
+ * space, one persistent fused forward + L1 + adjoint launch over all tiles,
+ * Adam, clamps. Stream-ordered, no host synchronisation, graph-capturable
+ * after igs_batch_setup. tuning may be NULL (defaults). d_loss_out
+ * (nullable, device float [B]) receives each image's mean L1 loss. */
+int igs_fit_batch_step(const igs_fit_state* st, const float* d_targets,
+                       const igs_batch_shape* shape, const igs_config* cfg,
+                       const igs_batch_tuning* tuning, void* ws, size_t ws_bytes,
+                       int64_t m_capacity, float* d_loss_out, igs_stream stream);
+
+/* Chooses the persistent adjoint's mapping for this batch by timing every
+ * candidate (CTAs per SM x stage x order) on the current parameters: bins
+ * once, runs each candidate `reps` times, keeps the fastest. Parameters and
+ * Adam state are not modified (st->grad is used as scratch). Synchronises
+ * `stream`. best_ms (nullable, host) receives the winner's mean time. */
+int igs_autotune_batch(const igs_fit_state* st, const float* d_targets,
+                       const igs_batch_shape* shape, const igs_config* cfg, void* ws,
+                       size_t ws_bytes, int64_t m_capacity, int32_t reps,
+                       igs_batch_tuning* best, float* best_ms, igs_stream stream);
+
 /* Forward render that allocates nothing and takes no workspace. The paper
  * has no counterpart: this is a convenience for callers that cannot call
  * cudaMalloc or hand the library a device buffer -- a plug-in inside a host

@@ -45,7 +45,23 @@ __global__ void k_finalize(int32_t* step, DevStatus* st, float inv_count, float*
   }
 }
 
+__global__ void k_finalize_batch(int32_t* step, const double* loss, const int4* dims, int B, int n,
+                                 float* loss_out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b == 0) *step += 1;
+  if (loss_out && b < B) {
+    const int4 d = dims[b];
+    loss_out[b] = (float)(loss[b] / ((double)d.x * d.y * n));
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_finalize_batch(int32_t* step, const double* loss, const int4* dims, int B,
+                                  int n, float* loss_out, cudaStream_t s) {
+  k_finalize_batch<<<(B + 255) / 256, 256, 0, s>>>(step, loss, dims, B, n, loss_out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_adam(const AdamParams& a, cudaStream_t s) {
   const int64_t total = a.N * (5 + a.n);

@@ -47,10 +47,16 @@ static int bits_for(int64_t x) {  // bits needed to represent values 0..x
 }
 
 WsLayout ws_layout(int64_t N, int n, int H, int W, int tile, int64_t m_cap) {
-  WsLayout L;
+  WsLayout L = ws_layout_tiles(N, n, (int64_t)((W + tile - 1) / tile) * ((H + tile - 1) / tile),
+                               m_cap);
   L.tiles_x = (W + tile - 1) / tile;
   L.tiles_y = (H + tile - 1) / tile;
-  const int64_t T = (int64_t)L.tiles_x * L.tiles_y;
+  return L;
+}
+
+WsLayout ws_layout_tiles(int64_t N, int n, int64_t T, int64_t m_cap) {
+  WsLayout L;
+  L.tiles_x = L.tiles_y = 0;
   L.passes = T <= 1 ? 0 : (bits_for(T - 1) + RADIX_BITS - 1) / RADIX_BITS;
   L.hist_blocks = m_cap > 0 ? (m_cap + RADIX_ITEMS - 1) / RADIX_ITEMS : 1;
   const int64_t pn = (N + SCAN_ITEMS - 1) / SCAN_ITEMS;

@@ -32,10 +32,23 @@ __device__ __forceinline__ void tile_span(float m, float r, int tile, int tiles,
   hi = (int)b;
 }
 
-template <typename T>
+// Image geometry of Gaussian i: the single image, or its image in a batch.
+struct ImgGeo {
+  int H, W, tiles_x, tiles_y, tile_base;
+};
+template <bool BATCH>
+__device__ __forceinline__ ImgGeo image_geo(const PrepParams& p, int64_t i) {
+  if (!BATCH) return ImgGeo{p.H, p.W, p.tiles_x, p.tiles_y, 0};
+  const int b = p.img_of[i];
+  const int4 d = p.img_dims[b];
+  return ImgGeo{d.x, d.y, d.z, d.w, p.tile_off[b]};
+}
+
+template <typename T, bool BATCH>
 __global__ void __launch_bounds__(256) k_preprocess(PrepParams p) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p.N) return;
+  const ImgGeo ig = image_geo<BATCH>(p, i);
   const T* xy = static_cast<const T*>(p.xy) + i * p.xy_stride;
   const T* ts = static_cast<const T*>(p.inv_scale) + i * p.inv_scale_stride;
   const T* cp = static_cast<const T*>(p.color) + i * p.color_stride;
@@ -52,8 +65,8 @@ __global__ void __launch_bounds__(256) k_preprocess(PrepParams p) {
   }
   if (!(ok && cok)) atomicOr(&p.status->flags, FLAG_NONFINITE);
 
-  const float mx = __fmul_rn(mux, (float)p.W);
-  const float my = __fmul_rn(muy, (float)p.H);
+  const float mx = __fmul_rn(mux, (float)ig.W);
+  const float my = __fmul_rn(muy, (float)ig.H);
   double sd, cd;
   sincos((double)th, &sd, &cd);
   const float c = __double2float_rn(cd), s = __double2float_rn(sd);
@@ -63,13 +76,13 @@ __global__ void __launch_bounds__(256) k_preprocess(PrepParams p) {
   unsigned int count = 0;
   if (ok && isfinite(mx) && isfinite(my) && isfinite(r)) {
     int x0, x1, y0, y1;
-    tile_span(mx, r, p.tile, p.tiles_x, x0, x1);
-    tile_span(my, r, p.tile, p.tiles_y, y0, y1);
+    tile_span(mx, r, p.tile, ig.tiles_x, x0, x1);
+    tile_span(my, r, p.tile, ig.tiles_y, y0, y1);
     const float r2 = __fmul_rn(r, r);
     for (int ty = y0; ty <= y1; ++ty) {
-      const float Y0 = (float)(ty * p.tile), Y1 = (float)min((ty + 1) * p.tile, p.H);
+      const float Y0 = (float)(ty * p.tile), Y1 = (float)min((ty + 1) * p.tile, ig.H);
       for (int tx = x0; tx <= x1; ++tx) {
-        const float X0 = (float)(tx * p.tile), X1 = (float)min((tx + 1) * p.tile, p.W);
+        const float X0 = (float)(tx * p.tile), X1 = (float)min((tx + 1) * p.tile, ig.W);
         count += circle_hits_rect(mx, my, r2, X0, X1, Y0, Y1) ? 1u : 0u;
       }
     }
@@ -84,27 +97,29 @@ __global__ void __launch_bounds__(256) k_preprocess(PrepParams p) {
   p.cnt[i] = count;
 }
 
+template <bool BATCH>
 __global__ void __launch_bounds__(256) k_emit(PrepParams p) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0 && p.status->m_needed > (unsigned long long)p.m_cap)
     atomicOr(&p.status->flags, FLAG_CAPACITY);
   if (i >= p.N) return;
+  const ImgGeo ig = image_geo<BATCH>(p, i);
   const GRec g = p.rec[i];
   const float mx = g.a.x, my = g.a.y, r = g.b.y;
   if (!(r >= 0.0f) || !isfinite(mx) || !isfinite(my) || !isfinite(r)) return;
   unsigned long long pos = p.off[i];
   int x0, x1, y0, y1;
-  tile_span(mx, r, p.tile, p.tiles_x, x0, x1);
-  tile_span(my, r, p.tile, p.tiles_y, y0, y1);
+  tile_span(mx, r, p.tile, ig.tiles_x, x0, x1);
+  tile_span(my, r, p.tile, ig.tiles_y, y0, y1);
   const float r2 = __fmul_rn(r, r);
   const unsigned long long cap = (unsigned long long)p.m_cap;
   for (int ty = y0; ty <= y1; ++ty) {
-    const float Y0 = (float)(ty * p.tile), Y1 = (float)min((ty + 1) * p.tile, p.H);
+    const float Y0 = (float)(ty * p.tile), Y1 = (float)min((ty + 1) * p.tile, ig.H);
     for (int tx = x0; tx <= x1; ++tx) {
-      const float X0 = (float)(tx * p.tile), X1 = (float)min((tx + 1) * p.tile, p.W);
+      const float X0 = (float)(tx * p.tile), X1 = (float)min((tx + 1) * p.tile, ig.W);
       if (circle_hits_rect(mx, my, r2, X0, X1, Y0, Y1)) {
         if (pos < cap) {
-          p.keys[pos] = (unsigned int)(ty * p.tiles_x + tx);
+          p.keys[pos] = (unsigned int)(ig.tile_base + ty * ig.tiles_x + tx);
           p.vals[pos] = (unsigned int)i;
         }
         ++pos;
@@ -329,15 +344,56 @@ __global__ void __launch_bounds__(256) k_tile_evals(const int2* range, int T, in
   if (threadIdx.x == 0 && tot) atomicAdd(&st->evals, tot);
 }
 
+__global__ void __launch_bounds__(256) k_fill_image_of(int* img_of, const long long* off,
+                                                       int B, int64_t N) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = B - 1;  // largest b with off[b] <= i
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    img_of[i] = lo;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_tile_evals_batch(const int2* range, int T,
+                                                          const int4* dims, const int* tile_off,
+                                                          int B, int tile, DevStatus* st) {
+  __shared__ unsigned long long s_warp[33];
+  unsigned long long acc = 0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < T; j += gridDim.x * blockDim.x) {
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_off[mid] <= j) lo = mid; else hi = mid - 1;
+    }
+    const int4 d = dims[lo];
+    const int local = j - tile_off[lo];
+    const int tx = local % d.z, ty = local / d.z;
+    const int w = min((tx + 1) * tile, d.y) - tx * tile;
+    const int h = min((ty + 1) * tile, d.x) - ty * tile;
+    const int2 r = range[j];
+    acc += (unsigned long long)(r.y - r.x) * (unsigned long long)(w * h);
+  }
+  unsigned long long tot;
+  block_exclusive_scan<unsigned long long>(acc, s_warp, tot);
+  if (threadIdx.x == 0 && tot) atomicAdd(&st->evals, tot);
+}
+
 }  // namespace
 
 cudaError_t launch_preprocess(const PrepParams& p, int dtype, cudaStream_t s) {
   if (p.N == 0) return cudaSuccess;
   const unsigned grid = (unsigned)((p.N + 255) / 256);
-  switch (dtype) {
-    case 0: k_preprocess<float><<<grid, 256, 0, s>>>(p); break;
-    case 1: k_preprocess<__half><<<grid, 256, 0, s>>>(p); break;
-    case 2: k_preprocess<__nv_bfloat16><<<grid, 256, 0, s>>>(p); break;
+  const bool batch = p.img_of != nullptr;
+  switch (dtype * 2 + (batch ? 1 : 0)) {
+    case 0: k_preprocess<float, false><<<grid, 256, 0, s>>>(p); break;
+    case 1: k_preprocess<float, true><<<grid, 256, 0, s>>>(p); break;
+    case 2: k_preprocess<__half, false><<<grid, 256, 0, s>>>(p); break;
+    case 3: k_preprocess<__half, true><<<grid, 256, 0, s>>>(p); break;
+    case 4: k_preprocess<__nv_bfloat16, false><<<grid, 256, 0, s>>>(p); break;
+    case 5: k_preprocess<__nv_bfloat16, true><<<grid, 256, 0, s>>>(p); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -345,7 +401,27 @@ cudaError_t launch_preprocess(const PrepParams& p, int dtype, cudaStream_t s) {
 
 cudaError_t launch_emit(const PrepParams& p, cudaStream_t s) {
   const unsigned grid = (unsigned)((p.N + 255) / 256);
-  k_emit<<<grid > 0 ? grid : 1, 256, 0, s>>>(p);
+  if (p.img_of)
+    k_emit<true><<<grid > 0 ? grid : 1, 256, 0, s>>>(p);
+  else
+    k_emit<false><<<grid > 0 ? grid : 1, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_image_of(int* img_of, const long long* gauss_off, int B, int64_t N,
+                                 cudaStream_t s) {
+  if (N == 0) return cudaSuccess;
+  const int64_t want = (N + 255) / 256;
+  k_fill_image_of<<<(unsigned)std::min<int64_t>(want, 148 * 16), 256, 0, s>>>(img_of, gauss_off,
+                                                                              B, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_evals_batch(const int2* range, int T, const int4* dims,
+                                    const int* tile_off, int B, int tile, DevStatus* status,
+                                    cudaStream_t s) {
+  const unsigned g = (unsigned)std::min<int64_t>((T + 255) / 256, 148 * 4);
+  k_tile_evals_batch<<<g > 0 ? g : 1, 256, 0, s>>>(range, T, dims, tile_off, B, tile, status);
   return cudaGetLastError();
 }
 
@@ -385,8 +461,10 @@ cudaError_t launch_ranges(const unsigned int* keys, int2* range, int T, int64_t 
   int64_t want = (m_cap + 255) / 256;
   const unsigned grid = (unsigned)(want < 148 * 8 ? (want > 0 ? want : 1) : 148 * 8);
   k_ranges<<<grid, 256, 0, s>>>(keys, range, T, status, m_cap);
-  const unsigned g2 = (unsigned)std::min<int64_t>((T + 255) / 256, 148 * 4);
-  k_tile_evals<<<g2 > 0 ? g2 : 1, 256, 0, s>>>(range, T, H, W, tile, tiles_x, status);
+  if (tiles_x > 0) {  // single image; the batched form counts its evaluations itself
+    const unsigned g2 = (unsigned)std::min<int64_t>((T + 255) / 256, 148 * 4);
+    k_tile_evals<<<g2 > 0 ? g2 : 1, 256, 0, s>>>(range, T, H, W, tile, tiles_x, status);
+  }
   return cudaGetLastError();
 }
 

@@ -29,6 +29,8 @@ struct WsLayout {
   int tiles_x, tiles_y, passes;
 };
 WsLayout ws_layout(int64_t N, int n, int H, int W, int tile, int64_t m_cap);
+// Same layout for T tiles in total (batched form: tiles of all images).
+WsLayout ws_layout_tiles(int64_t N, int n, int64_t T, int64_t m_cap);
 // Sets the calling thread's message returned by igs_last_error.
 void set_last_error(const char* msg);
 
@@ -49,6 +51,11 @@ struct PrepParams {
   unsigned int* vals;
   int64_t m_cap;
   DevStatus* status;
+  // batched form: image of each Gaussian, per-image (H, W, tiles_x, tiles_y)
+  // and first global tile; all null for a single image
+  const int* img_of;
+  const int4* img_dims;
+  const int* tile_off;
 };
 
 struct RenderParams {
@@ -72,8 +79,26 @@ struct RenderParams {
   int tile;
 };
 
+// Per-image tables of the batched form (device, inside the workspace).
+struct BatchTables {
+  int B;
+  const int4* dims;            // (H, W, tiles_x, tiles_y) per image
+  const int* tile_off;         // [B+1] first global tile of each image
+  const long long* pix_off;    // [B+1] offset (floats) of each image's planes
+  double* loss;                // [B] sum |c_r - c_t| per image
+  unsigned int* work;          // next work item (tile) counter, zeroed per launch
+  int T;                       // total tiles
+  int order;                   // 0: dynamic counter, 1: static round-robin
+};
+
 cudaError_t launch_preprocess(const PrepParams& p, int dtype, cudaStream_t s);
 cudaError_t launch_emit(const PrepParams& p, cudaStream_t s);
+// Batched form: image index of every Gaussian from the per-image offsets.
+cudaError_t launch_fill_image_of(int* img_of, const long long* gauss_off, int B, int64_t N,
+                                 cudaStream_t s);
+cudaError_t launch_tile_evals_batch(const int2* range, int T, const int4* dims,
+                                    const int* tile_off, int B, int tile, DevStatus* status,
+                                    cudaStream_t s);
 // Exclusive scan of n u32 counts into u64 offsets; total goes to *total.
 cudaError_t launch_scan_u32_to_u64(const unsigned int* in, unsigned long long* out, int64_t n,
                                    unsigned long long* part, unsigned long long* total,
@@ -90,6 +115,9 @@ cudaError_t launch_ranges(const unsigned int* keys, int2* range, int T, int64_t 
 // Render family: return cudaErrorInvalidValue for an unsupported (tile, K, n).
 cudaError_t launch_render_fwd(const RenderParams& p, int tile, int K, cudaStream_t s);
 cudaError_t launch_render_bwd(const RenderParams& p, int tile, int K, cudaStream_t s);
+// Persistent adjoint over a batch of images (16x16 tiles); stage in {64,128,256}.
+cudaError_t launch_render_bwd_batch(const RenderParams& p, const BatchTables& bt, int K,
+                                    int stage, int grid, cudaStream_t s);
 cudaError_t launch_decode(const RenderParams& p, int K, cudaStream_t s);
 bool render_supported(int tile, int K, int n);
 
@@ -108,5 +136,8 @@ struct AdamParams {
 cudaError_t launch_adam(const AdamParams& a, cudaStream_t s);
 cudaError_t launch_finalize(int32_t* step, DevStatus* status, float inv_count, float* loss_out,
                             cudaStream_t s);
+// Batched form: step counter and per-image mean L1 loss.
+cudaError_t launch_finalize_batch(int32_t* step, const double* loss, const int4* dims, int B,
+                                  int n, float* loss_out, cudaStream_t s);
 
 }  // namespace igs

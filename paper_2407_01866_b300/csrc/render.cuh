@@ -64,18 +64,18 @@ __device__ __forceinline__ void stage_chunk(const RenderParams& p, int base, int
   }
 }
 
-// Pass A: the K smallest keys at (px, py), ascending.
-template <int TILE, int K>
+// Pass A: the K smallest keys at (px, py), ascending. CH list entries are
+// staged per round ("Gaussians per stage", CH <= TILE*TILE).
+template <int TILE, int K, int CH>
 __device__ __forceinline__ void select_keys(const RenderParams& p, int2 range, float px,
                                             float py, float (&tq)[K], float4* s_a, float* s_a11,
                                             int* s_gid) {
-  constexpr int NT = TILE * TILE;
 #pragma unroll
   for (int k = 0; k < K; ++k) tq[k] = F_INF;
-  for (int base = range.x; base < range.y; base += NT) {
-    const int cnt = min(NT, range.y - base);
+  for (int base = range.x; base < range.y; base += CH) {
+    const int cnt = min(CH, range.y - base);
     __syncthreads();
-    stage_chunk<NT>(p, base, cnt, s_a, s_a11, s_gid);
+    stage_chunk<CH>(p, base, cnt, s_a, s_a11, s_gid);
     __syncthreads();
 #pragma unroll 4
     for (int j = 0; j < cnt; ++j) {
@@ -106,12 +106,11 @@ struct PixelBlend {
 };
 
 // Pass B: exact top-K membership in list order and the blend of Eq. 5.
-template <int TILE, int K, int NC>
+template <int TILE, int K, int NC, int CH>
 __device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, float px,
                                            float py, const float (&tq)[K],
                                            PixelBlend<Chan<NC>::R>& r, float4* s_a,
                                            float* s_a11, int* s_gid) {
-  constexpr int NT = TILE * TILE;
   constexpr int NCR = Chan<NC>::R;
   const int n = nchan<NC>(p);
   r.q0 = tq[0];
@@ -124,10 +123,10 @@ __device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, fl
   r.Z = 0.0f;
 #pragma unroll
   for (int c = 0; c < NCR; ++c) r.cr[c] = 0.0f;
-  for (int base = range.x; base < range.y; base += NT) {
-    const int cnt = min(NT, range.y - base);
+  for (int base = range.x; base < range.y; base += CH) {
+    const int cnt = min(CH, range.y - base);
     __syncthreads();
-    stage_chunk<NT>(p, base, cnt, s_a, s_a11, s_gid);
+    stage_chunk<CH>(p, base, cnt, s_a, s_a11, s_gid);
     __syncthreads();
     const int rel = base - range.x;
 #pragma unroll 2
@@ -170,9 +169,9 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(RenderParams p) {
   const float px = (float)x + 0.5f, py = (float)y + 0.5f;
   const int2 range = p.range[tile_id];
   float tq[K];
-  select_keys<TILE, K>(p, range, px, py, tq, s_a, s_a11, s_gid);
+  select_keys<TILE, K, NT>(p, range, px, py, tq, s_a, s_a11, s_gid);
   PixelBlend<Chan<NC>::R> r;
-  blend_pass<TILE, K, NC>(p, range, px, py, tq, r, s_a, s_a11, s_gid);
+  blend_pass<TILE, K, NC, NT>(p, range, px, py, tq, r, s_a, s_a11, s_gid);
   if (x >= p.W || y >= p.H) return;
   const int n = nchan<NC>(p);
   const int64_t plane = (int64_t)p.H * p.W;
@@ -201,11 +200,21 @@ __host__ __device__ inline BwdSmem bwd_smem(int NT, int n) {
   return L;
 }
 
-template <int TILE, int K, int NC>
-__global__ void __launch_bounds__(TILE * TILE) k_render_bwd(RenderParams p) {
+// Where one tile of one image lives (the batched form renders many images).
+struct TileCtx {
+  int2 range;        // [start, end) of the tile's list
+  int x0, y0;        // tile origin in pixels
+  int H, W;          // its image
+  int64_t off;       // offset (floats) of the image in img / target / grad_img
+  float inv_count;   // 1 / (H W n)
+  double* loss_acc;  // where the tile adds sum |c_r - c_t|
+};
+
+// Adjoint of one tile: passes A and B per pixel, then pass C per candidate.
+template <int TILE, int K, int NC, int CH>
+__device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t, float* smem) {
   constexpr int NT = TILE * TILE;
   constexpr int NCR = Chan<NC>::R;
-  extern __shared__ __align__(16) float smem[];
   const int n = nchan<NC>(p);
   const BwdSmem SL = bwd_smem(NT, n);
   float4* s_a = reinterpret_cast<float4*>(smem + SL.a);
@@ -217,26 +226,23 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(RenderParams p) {
   float* s_part = smem + SL.part;
   double* s_loss = reinterpret_cast<double*>(smem + SL.loss);
 
-  const int tile_id = blockIdx.x;
-  const int tx = tile_id % p.tiles_x, ty = tile_id / p.tiles_x;
   const int2 lp = pixel_of<TILE>(threadIdx.x);
-  const int x = tx * TILE + lp.x, y = ty * TILE + lp.y;
+  const int x = t.x0 + lp.x, y = t.y0 + lp.y;
   const float px = (float)x + 0.5f, py = (float)y + 0.5f;
-  const int2 range = p.range[tile_id];
-  const int len = range.y - range.x;
+  const int2 range = t.range;
 
   // ---- passes A and B: per-pixel forward values and upstream gradient
   float tq[K];
-  select_keys<TILE, K>(p, range, px, py, tq, s_a, s_a11, s_gid);
+  select_keys<TILE, K, CH>(p, range, px, py, tq, s_a, s_a11, s_gid);
   PixelBlend<NCR> r;
-  blend_pass<TILE, K, NC>(p, range, px, py, tq, r, s_a, s_a11, s_gid);
+  blend_pass<TILE, K, NC, CH>(p, range, px, py, tq, r, s_a, s_a11, s_gid);
 
   float loss = 0.0f;
-  const bool live = x < p.W && y < p.H && r.Z > 0.0f;
+  const bool live = x < t.W && y < t.H && r.Z > 0.0f;
   float beta = 0.0f;
   const float iz = live ? 1.0f / r.Z : 0.0f;
-  const int64_t plane = (int64_t)p.H * p.W;
-  const int64_t o = (int64_t)y * p.W + x;
+  const int64_t plane = (int64_t)t.H * t.W;
+  const int64_t o = t.off + (int64_t)y * t.W + x;
 #pragma unroll
   for (int c = 0; c < NCR; ++c) {
     if (NC > 0 || c < n) {
@@ -247,7 +253,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(RenderParams p) {
         } else {
           const float d = r.cr[c] - p.target[c * plane + o];
           loss += fabsf(d);
-          g = sign_f(d) * p.inv_count;
+          g = sign_f(d) * t.inv_count;
         }
       }
       const float gh = -0.5f * g * iz;  // dL/dq_k = w_k * (sum_c gh_c c_k,c - beta)
@@ -263,15 +269,15 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(RenderParams p) {
   }
   __syncthreads();
   if (!p.grad_img && threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < NT / 32; ++i) t += s_loss[i];
-    if (t != 0.0) atomicAdd(&p.status->loss_sum, t);
+    double tot = 0.0;
+    for (int i = 0; i < NT / 32; ++i) tot += s_loss[i];
+    if (tot != 0.0) atomicAdd(t.loss_acc, tot);
   }
 
   // ---- pass C: candidate-major accumulation of the adjoint
   const int np = 5 + n;
-  for (int cbase = range.x; cbase < range.y; cbase += NT) {
-    const int C = min(NT, range.y - cbase);
+  for (int cbase = range.x; cbase < range.y; cbase += CH) {
+    const int C = min(CH, range.y - cbase);
     const int G = max(1, NT / C);            // pixel groups per candidate
     const int PPG = (NT + G - 1) / G;        // pixels per group
     const int j = (int)threadIdx.x % C;
@@ -293,6 +299,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(RenderParams p) {
       for (int i = i0; i < i1; ++i) {
         const float4 s0 = s_ps0[i];
         const float2 s1 = s_ps1[i];
+        // the ranking key of pass A, recomputed bit for bit (same sequence)
         const float dx = __fsub_rn(s0.x, rc.a.x);
         const float dy = __fsub_rn(s0.y, rc.a.y);
         const float h = __fmaf_rn(rc.a.w, dy, __fmul_rn(rc.a.z, dx));
@@ -348,8 +355,8 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(RenderParams p) {
       const float dT2 = T[2] * s2 + T[4] * c2 - 2.0f * T[3] * sc;
       const float d_th = (T1 - T2) * (2.0f * sc * (T[4] - T[2]) + 2.0f * (c2 - s2) * T[3]);
       float* gdst = p.grad + (int64_t)gid * np;
-      atomicAdd(gdst + 0, d_mx * (float)p.W);
-      atomicAdd(gdst + 1, d_my * (float)p.H);
+      atomicAdd(gdst + 0, d_mx * (float)t.W);
+      atomicAdd(gdst + 1, d_my * (float)t.H);
       atomicAdd(gdst + 2, d_th);
       atomicAdd(gdst + 3, 2.0f * t1 * dT1);
       atomicAdd(gdst + 4, 2.0f * t2 * dT2);
@@ -361,7 +368,64 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(RenderParams p) {
     }
     __syncthreads();
   }
-  (void)len;
+}
+
+template <int TILE, int K, int NC>
+__global__ void __launch_bounds__(TILE * TILE) k_render_bwd(RenderParams p) {
+  extern __shared__ __align__(16) float smem[];
+  const int tile_id = blockIdx.x;
+  TileCtx t;
+  t.range = p.range[tile_id];
+  t.x0 = (tile_id % p.tiles_x) * TILE;
+  t.y0 = (tile_id / p.tiles_x) * TILE;
+  t.H = p.H;
+  t.W = p.W;
+  t.off = 0;
+  t.inv_count = p.inv_count;
+  t.loss_acc = &p.status->loss_sum;
+  bwd_tile<TILE, K, NC, TILE * TILE>(p, t, smem);
+}
+
+__device__ __forceinline__ int image_of_tile(const BatchTables& bt, int tile) {
+  int lo = 0, hi = bt.B - 1;  // largest b with tile_off[b] <= tile
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (bt.tile_off[mid] <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Persistent adjoint over the concatenated tiles of many images: each CTA
+// pulls tiles until none is left (no inter-CTA waits).
+template <int TILE, int K, int NC, int CH>
+__global__ void __launch_bounds__(TILE * TILE) k_render_bwd_batch(RenderParams p,
+                                                                  BatchTables bt) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ int s_item;
+  int it = blockIdx.x;
+  for (;;) {
+    if (bt.order == 0) {
+      if (threadIdx.x == 0) s_item = (int)atomicAdd(bt.work, 1u);
+      __syncthreads();
+      it = s_item;
+      __syncthreads();
+    }
+    if (it >= bt.T) break;
+    const int b = image_of_tile(bt, it);
+    const int4 dm = bt.dims[b];
+    const int local = it - bt.tile_off[b];
+    TileCtx t;
+    t.range = p.range[it];
+    t.x0 = (local % dm.z) * TILE;
+    t.y0 = (local / dm.z) * TILE;
+    t.H = dm.x;
+    t.W = dm.y;
+    t.off = bt.pix_off[b];
+    t.inv_count = 1.0f / ((float)dm.x * (float)dm.y * (float)nchan<NC>(p));
+    t.loss_acc = bt.loss + b;
+    bwd_tile<TILE, K, NC, CH>(p, t, smem);
+    if (bt.order != 0) it += gridDim.x;
+  }
 }
 
 // One thread per query point: its tile's list is walked from global memory.

@@ -65,6 +65,20 @@ class FitState(ctypes.Structure):
                 ("step", ctypes.c_void_p), ("N", ctypes.c_int64), ("n", ctypes.c_int32)]
 
 
+class BatchShape(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("H", ctypes.POINTER(ctypes.c_int32)), ("W", ctypes.POINTER(ctypes.c_int32)),
+                ("N", ctypes.POINTER(ctypes.c_int64))]
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int32), ("stage", ctypes.c_int32),
+                ("order", ctypes.c_int32)]
+
+    def __repr__(self):
+        return f"BatchTuning(ctas_per_sm={self.ctas_per_sm}, stage={self.stage}, order={self.order})"
+
+
 _P = ctypes.c_void_p
 _SIGNATURES = {
     "igs_version": ([], ctypes.c_int),
@@ -89,6 +103,17 @@ _SIGNATURES = {
     "igs_render_forward_static": ([ctypes.POINTER(Gaussians), ctypes.c_int32, ctypes.c_int32,
                                    ctypes.POINTER(Config), _P, _P], ctypes.c_int),
     "igs_static_scratch_bytes": ([ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "igs_batch_workspace_size": ([ctypes.POINTER(BatchShape), ctypes.POINTER(Config),
+                                  ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "igs_batch_setup": ([ctypes.POINTER(BatchShape), ctypes.POINTER(Config), _P, ctypes.c_size_t,
+                         ctypes.c_int64, _P], ctypes.c_int),
+    "igs_fit_batch_step": ([ctypes.POINTER(FitState), _P, ctypes.POINTER(BatchShape),
+                            ctypes.POINTER(Config), ctypes.POINTER(BatchTuning), _P,
+                            ctypes.c_size_t, ctypes.c_int64, _P, _P], ctypes.c_int),
+    "igs_autotune_batch": ([ctypes.POINTER(FitState), _P, ctypes.POINTER(BatchShape),
+                            ctypes.POINTER(Config), _P, ctypes.c_size_t, ctypes.c_int64,
+                            ctypes.c_int32, ctypes.POINTER(BatchTuning),
+                            ctypes.POINTER(ctypes.c_float), _P], ctypes.c_int),
 }
 
 _lib = None
@@ -224,6 +249,47 @@ def static_scratch_bytes():
     b = ctypes.c_size_t(0)
     _check(load().igs_static_scratch_bytes(ctypes.byref(b)))
     return b.value
+
+
+def batch_shape(Hs, Ws, Ns, n):
+    """igs_batch_shape over host arrays (kept alive on the returned struct)."""
+    B = len(Hs)
+    h = (ctypes.c_int32 * B)(*[int(v) for v in Hs])
+    w = (ctypes.c_int32 * B)(*[int(v) for v in Ws])
+    m = (ctypes.c_int64 * B)(*[int(v) for v in Ns])
+    sh = BatchShape(B, n, h, w, m)
+    sh._keep = (h, w, m)
+    return sh
+
+
+def batch_workspace_size(shape, cfg, m_capacity):
+    b = ctypes.c_size_t(0)
+    _check(load().igs_batch_workspace_size(ctypes.byref(shape), ctypes.byref(cfg), m_capacity,
+                                           ctypes.byref(b)))
+    return b.value
+
+
+def batch_setup(shape, cfg, ws, m_capacity, stream=None):
+    _check(load().igs_batch_setup(ctypes.byref(shape), ctypes.byref(cfg), _ptr(ws), ws.numel(),
+                                  m_capacity, _stream(stream)))
+
+
+def fit_batch_step(state, targets, shape, cfg, ws, m_capacity, tuning=None, loss_out=None,
+                   stream=None):
+    tp = ctypes.byref(tuning) if tuning is not None else None
+    _check(load().igs_fit_batch_step(ctypes.byref(state), _ptr(targets), ctypes.byref(shape),
+                                     ctypes.byref(cfg), tp, _ptr(ws), ws.numel(), m_capacity,
+                                     _ptr(loss_out), _stream(stream)))
+
+
+def autotune_batch(state, targets, shape, cfg, ws, m_capacity, reps=3, stream=None):
+    """Times every persistent-adjoint mapping on this batch; returns (tuning, ms)."""
+    best = BatchTuning()
+    ms = ctypes.c_float(0)
+    _check(load().igs_autotune_batch(ctypes.byref(state), _ptr(targets), ctypes.byref(shape),
+                                     ctypes.byref(cfg), _ptr(ws), ws.numel(), m_capacity, reps,
+                                     ctypes.byref(best), ctypes.byref(ms), _stream(stream)))
+    return best, ms.value
 
 
 def read_stats(bins, stream=None):
