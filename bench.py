@@ -25,6 +25,11 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(name="fit2048_rgb", H=2048, W=2048, n=3, N=100_000, n_sin=8, n_rect=200,
                 noise=3, seed=0)
+FIT_WORKLOADS = {
+    "fit2048_rgb": WORKLOAD,
+    "fit4096_tex9": dict(name="fit4096_tex9", H=4096, W=4096, n=9, N=500_000, n_sin=8,
+                         n_rect=200, noise=3, seed=0),
+}
 METRIC = "Gaussian-pixel evals/s and fit steps/s (fwd+bwd) vs FP32/SFU roofline"
 UNIT = "fit steps/s"
 SM_COUNT = 148
@@ -90,20 +95,24 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
-def make_inputs():
+def make_inputs(w=WORKLOAD):
     from paper_2407_01866_b300 import synth
-    w = WORKLOAD
-    target = synth.target_image(w["H"], w["W"], w["n"], seed=w["seed"], n_sin=w["n_sin"],
-                                n_rect=w["n_rect"], noise_octaves=w["noise"])
-    d = synth.gaussians(w["N"], w["n"], seed=w["seed"])
+    if w["n"] == 9:   # albedo RGB, normal XYZ in [-1, 1], roughness, metallic, AO
+        target = synth.texture_stack(w["H"], w["W"], seed=w["seed"], n_sin=w["n_sin"],
+                                     n_rect=w["n_rect"], noise_octaves=w["noise"])
+        lo = [0, 0, 0, -1, -1, -1, 0, 0, 0]
+        d = synth.gaussians(w["N"], 9, seed=w["seed"], color_lo=lo, color_hi=1.0)
+    else:
+        target = synth.target_image(w["H"], w["W"], w["n"], seed=w["seed"], n_sin=w["n_sin"],
+                                    n_rect=w["n_rect"], noise_octaves=w["noise"])
+        d = synth.gaussians(w["N"], w["n"], seed=w["seed"])
     return target, synth.packed(d)
 
 
-def cpu_baseline(target, P, budget_s=15.0, seed=0):
+def cpu_baseline(target, P, budget_s=15.0, seed=0, w=WORKLOAD):
     """Oracle fit step (forward + L1 + adjoint over sampled pixels), extrapolated."""
     from oracle import image_gs as O
     from paper_2407_01866_b300 import synth
-    w = WORKLOAD
     H, W, n = w["H"], w["W"], w["n"]
     g = O.Gaussians.from_packed(P)
     pix = synth.sample_pixels(4096, H, W, seed=seed)
@@ -121,8 +130,8 @@ def cpu_baseline(target, P, budget_s=15.0, seed=0):
     per_pixel = dt / done
     step_s = per_pixel * H * W
     return {"value": 1.0 / step_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} random pixels of the 2048x2048 workload, forward + L1 + adjoint "
-                      f"brute force in float64 over all 100k Gaussians ({dt:.1f} s), "
+            "sample": f"{done} random pixels of the {H}x{W} workload, forward + L1 + adjoint "
+                      f"brute force in float64 over all {w['N']} Gaussians ({dt:.1f} s), "
                       "extrapolated to the full frame"}
 
 
@@ -151,7 +160,7 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def run_ours(args):
+def run_ours(args, w=WORKLOAD):
     import torch
     from paper_2407_01866_b300 import lib as L
 
@@ -164,9 +173,8 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = WORKLOAD
     H, W, n, N = w["H"], w["W"], w["n"], w["N"]
-    target_np, P_np = make_inputs()
+    target_np, P_np = make_inputs(w)
     cfg = L.default_config()
     target = torch.from_numpy(target_np).to(dev)
     P0 = torch.from_numpy(P_np).to(dev)
@@ -297,10 +305,172 @@ def run_ours(args):
             "clocks": clocks.summary(),
         }
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(target_np, P_np, budget_s=args.cpu_budget)
+            line["cpu_baseline"] = cpu_baseline(target_np, P_np, budget_s=args.cpu_budget, w=w)
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
+
+
+def _time_events(fn, steps, flush=None):
+    """Mean ms of fn() over `steps` runs, CUDA events on the current stream."""
+    import torch
+    st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        if flush is not None:
+            flush.fill_(i & 0xff)
+        st[i].record()
+        fn()
+        en[i].record()
+    torch.cuda.synchronize()
+    return float(statistics.mean(a.elapsed_time(b) for a, b in zip(st, en)))
+
+
+def run_batch(args):
+    """64 images, sides log-uniform in 256-2048, one Gaussian per 28 px: batched
+    persistent fit step (autotuned mapping) vs 64 single-image fit steps, both
+    replayed from CUDA graphs."""
+    import torch
+    from paper_2407_01866_b300 import lib as L
+    from paper_2407_01866_b300 import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    shapes = synth.batch_shapes(64, seed=0)
+    Hs = [h for h, _, _ in shapes]
+    Ws = [w for _, w, _ in shapes]
+    Ns = [m for _, _, m in shapes]
+    n = 3
+    cfg = L.default_config()
+    Ps = [synth.packed(synth.gaussians(N, n, seed=b)) for b, N in enumerate(Ns)]
+    Ts = [synth.target_image(H, W, n, seed=100 + b, n_rect=20) for b, (H, W) in
+          enumerate(zip(Hs, Ws))]
+    P_all = torch.from_numpy(np.concatenate(Ps)).to(dev)
+    T_all = torch.from_numpy(np.concatenate([t.ravel() for t in Ts])).to(dev)
+
+    def state(P):
+        G, m, v = torch.zeros_like(P), torch.zeros_like(P), torch.zeros_like(P)
+        step = torch.zeros(1, dtype=torch.int32, device=dev)
+        keep = (P, G, m, v, step)
+        s_ = L.FitState(P.data_ptr(), G.data_ptr(), m.data_ptr(), v.data_ptr(),
+                        step.data_ptr(), P.shape[0], n)
+        s_._keep = keep
+        return s_
+
+    shape = L.batch_shape(Hs, Ws, Ns, n)
+    cap = 12 * sum(Ns) + 4096
+    ws = L.alloc_workspace(L.batch_workspace_size(shape, cfg, cap), dev)
+    L.batch_setup(shape, cfg, ws, cap)
+    Pb = P_all.clone()
+    sb = state(Pb)
+    loss_b = torch.zeros(64, device=dev)
+    tuning, tune_ms = L.autotune_batch(sb, T_all, shape, cfg, ws, cap, reps=3)
+
+    def capture(fn):
+        s_ = torch.cuda.Stream(device=dev)
+        s_.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s_):
+            fn()
+        torch.cuda.current_stream().wait_stream(s_)
+        g_ = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_):
+            fn()
+        return g_
+
+    gb = capture(lambda: L.fit_batch_step(sb, T_all, shape, cfg, ws, cap, tuning=tuning,
+                                          loss_out=loss_b))
+    # sequential: one plain fit step per image, all 64 in one graph
+    seq = []
+    off_p, off_t = 0, 0
+    for b in range(64):
+        N, H, W = Ns[b], Hs[b], Ws[b]
+        Pi = P_all[off_p:off_p + N].clone()
+        ti = T_all[off_t:off_t + n * H * W]
+        c = 12 * N + 1024
+        wsi = L.alloc_workspace(L.workspace_size(N, n, H, W, cfg, c), dev)
+        seq.append((state(Pi), ti, H, W, wsi, c, torch.zeros(1, device=dev)))
+        off_p += N
+        off_t += n * H * W
+
+    def seq_step():
+        for si, ti, H, W, wsi, c, li in seq:
+            L.fit_step(si, ti, H, W, cfg, wsi, c, li)
+
+    gs = capture(seq_step)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        gb.replay()
+        gs.replay()
+    torch.cuda.synchronize()
+    steps = min(args.steps, 100)
+    with ClockSampler(0) as clocks:
+        ms_b = _time_events(gb.replay, steps, flush)
+        ms_s = _time_events(gs.replay, steps, flush)
+    px = sum(h * w for h, w in zip(Hs, Ws))
+    line = {"metric": "images x fit steps/s (batched persistent form vs 64 sequential plain "
+                      "fit steps)", "value": 64 * 1000.0 / ms_b, "unit": "image-steps/s",
+            "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms_b,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "batch64", "images": 64, "pixels": px, "gaussians": sum(Ns),
+                       "sides": "log-uniform 256-2048", "K": cfg.K, "tile": cfg.tile,
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "tuning": {"ctas_per_sm": tuning.ctas_per_sm, "stage": tuning.stage,
+                       "order": tuning.order, "adjoint_ms": tune_ms},
+            "sequential": {"value": 64 * 1000.0 / ms_s, "ms_per_step": ms_s},
+            "speedup_vs_sequential": ms_s / ms_b,
+            "clocks": clocks.summary()}
+    print(json.dumps(line))
+
+
+def run_decode(args):
+    """8192x8192 RGB, 2M Gaussians: full-frame render and 1M random-point decode
+    with parameters stored as float32, float16 and bfloat16."""
+    import torch
+    from paper_2407_01866_b300 import lib as L
+    from paper_2407_01866_b300 import synth
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    c = synth.CONFIGS["decode8192_rgb"]
+    H, W, n, N, Q = c["H"], c["W"], c["n"], c["N"], c["Q"]
+    d = synth.gaussians(N, n, seed=0)
+    pts = torch.from_numpy(synth.query_points(Q, H, W, seed=0)).to(dev)
+    cfg = L.default_config()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    img = torch.empty((n, H, W), device=dev)
+    out = torch.empty((Q, n), device=dev)
+    res = {}
+    steps = min(args.steps, 50)
+    with ClockSampler(0) as clocks:
+        for name, dt in (("f32", torch.float32), ("f16", torch.float16), ("bf16", torch.bfloat16)):
+            ts = [torch.from_numpy(d[k]).to(dev).to(dt) for k in ("xy", "theta", "inv_scale",
+                                                                  "color")]
+            view = L.gaussians_view(*ts)
+            binner = L.Binner(N, n, H, W, cfg, m_capacity=8 * N)
+            bins = binner.bin(view)
+            st = L.read_stats(bins)
+            cap = binner.m_capacity
+            for _ in range(args.warmup):
+                L.preprocess_bin(view, H, W, cfg, binner.ws, cap)
+                L.render_forward(bins, cfg, img)
+                L.decode_points(bins, cfg, pts, out)
+            ms_bin = _time_events(lambda: L.preprocess_bin(view, H, W, cfg, binner.ws, cap),
+                                  steps, flush)
+            ms_fwd = _time_events(lambda: L.render_forward(bins, cfg, img), steps, flush)
+            ms_dec = _time_events(lambda: L.decode_points(bins, cfg, pts, out), steps, flush)
+            res[name] = {"bin_ms": ms_bin, "render_ms": ms_fwd, "frame_evals": int(st.evals),
+                         "render_evals_per_s": st.evals / (ms_fwd * 1e-3),
+                         "decode_ms": ms_dec, "queries_per_s": Q / (ms_dec * 1e-3),
+                         "param_bytes": sum(t.numel() * t.element_size() for t in ts)}
+    line = {"metric": "full-frame Gaussian-pixel evals/s and random-point queries/s by "
+                      "parameter storage", "value": res["f16"]["queries_per_s"],
+            "unit": "queries/s (f16 storage)", "n_gpus": 1, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": res["f16"]["decode_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 math, f16/bf16/f32 storage", "data": "synthetic",
+            "config": {"workload": "decode8192", "H": H, "W": W, "n": n, "N": N, "queries": Q,
+                       "l2": "flushed between timed launches (256 MB write)"},
+            "by_storage": res, "clocks": clocks.summary()}
+    print(json.dumps(line))
 
 
 def main():
@@ -311,6 +481,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--workload", default="fit2048_rgb",
+                    choices=list(FIT_WORKLOADS) + ["batch64", "decode8192"])
     ap.add_argument("--kernel-once", action="store_true",
                     help="bin, render and run the fused adjoint once, then exit (profiling)")
     args = ap.parse_args()
@@ -318,8 +490,12 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch64":
+        run_batch(args)
+    elif args.workload == "decode8192":
+        run_decode(args)
     else:
-        run_ours(args)
+        run_ours(args, FIT_WORKLOADS[args.workload])
 
 
 if __name__ == "__main__":
