@@ -9,6 +9,10 @@ namespace igs {
 
 namespace {
 
+// One thread per Gaussian row: the column of each element (and so its learning
+// rate and clamp) is known without a division, and a row's 5+n floats are
+// contiguous, so a warp touches 32 consecutive rows.
+template <int NP>
 __global__ void __launch_bounds__(256) k_adam(AdamParams a) {
   __shared__ float s_bc[2];
   if (threadIdx.x == 0) {
@@ -19,22 +23,26 @@ __global__ void __launch_bounds__(256) k_adam(AdamParams a) {
   __syncthreads();
   const float inv_bc1 = 1.0f / s_bc[0];
   const float inv_bc2 = 1.0f / s_bc[1];
-  const int np = 5 + a.n;
-  const int64_t total = a.N * np;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int col = (int)(i % np);
-    const float g = a.G[i];
-    const float m = a.b1 * a.m[i] + a.omb1 * g;
-    const float v = a.b2 * a.v[i] + a.omb2 * g * g;
-    const float lr = col < 2 ? a.lr_mu : col == 2 ? a.lr_theta : col < 5 ? a.lr_t : a.lr_c;
-    float p = a.P[i] - lr * (m * inv_bc1) / (sqrtf(v * inv_bc2) + a.eps);
-    if (col < 2) p = fminf(fmaxf(p, a.mu_min), a.mu_max);
-    else if (col == 2) p = fminf(fmaxf(p, a.theta_min), a.theta_max);
-    else if (col < 5) p = fminf(fmaxf(p, a.t_min), a.t_max);
-    a.P[i] = p;
-    a.m[i] = m;
-    a.v[i] = v;
+  const int np = NP > 0 ? NP : 5 + a.n;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.N;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t base = r * np;
+#pragma unroll
+    for (int col = 0; col < (NP > 0 ? NP : 64); ++col) {
+      if (NP == 0 && col >= np) break;
+      const int64_t i = base + col;
+      const float g = a.G[i];
+      const float m = a.b1 * a.m[i] + a.omb1 * g;
+      const float v = a.b2 * a.v[i] + a.omb2 * g * g;
+      const float lr = col < 2 ? a.lr_mu : col == 2 ? a.lr_theta : col < 5 ? a.lr_t : a.lr_c;
+      float p = a.P[i] - lr * (m * inv_bc1) / (sqrtf(v * inv_bc2) + a.eps);
+      if (col < 2) p = fminf(fmaxf(p, a.mu_min), a.mu_max);
+      else if (col == 2) p = fminf(fmaxf(p, a.theta_min), a.theta_max);
+      else if (col < 5) p = fminf(fmaxf(p, a.t_min), a.t_max);
+      a.P[i] = p;
+      a.m[i] = m;
+      a.v[i] = v;
+    }
   }
 }
 
@@ -64,11 +72,16 @@ cudaError_t launch_finalize_batch(int32_t* step, const double* loss, const int4*
 }
 
 cudaError_t launch_adam(const AdamParams& a, cudaStream_t s) {
-  const int64_t total = a.N * (5 + a.n);
-  if (total == 0) return cudaSuccess;
-  int64_t blocks = (total + 255) / 256;
+  if (a.N == 0) return cudaSuccess;
+  int64_t blocks = (a.N + 255) / 256;
   if (blocks > 148 * 16) blocks = 148 * 16;
-  k_adam<<<(unsigned)blocks, 256, 0, s>>>(a);
+  switch (a.n) {
+    case 1: k_adam<6><<<(unsigned)blocks, 256, 0, s>>>(a); break;
+    case 3: k_adam<8><<<(unsigned)blocks, 256, 0, s>>>(a); break;
+    case 4: k_adam<9><<<(unsigned)blocks, 256, 0, s>>>(a); break;
+    case 9: k_adam<14><<<(unsigned)blocks, 256, 0, s>>>(a); break;
+    default: k_adam<0><<<(unsigned)blocks, 256, 0, s>>>(a); break;
+  }
   return cudaGetLastError();
 }
 
