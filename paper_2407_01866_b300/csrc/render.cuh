@@ -157,73 +157,24 @@ __device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, fl
 }
 
 // ---------------------------------------------------------------------------
-// Fast path for tiles whose whole list fits one stage (the common case).
-//
-// Each warp orders the staged candidates by their key at the centre of its
-// 8 x 4 block, so that pass A meets the winners first and its insertion
-// network rarely runs late in the list. Pass A also records whether a
-// candidate whose key equals the final threshold tau was dropped (a boundary
-// tie). Without one, the winners are exactly the candidates with q <= tau,
-// and pass B walks the same order and stops once every lane of the warp has
-// found its K winners. A warp with a tie falls back to list order and the
-// exact (q, index) rule. Pass B's ballots give, per (warp block, candidate),
-// the mask of pixels where the candidate wins; the adjoint visits only those.
+// Adjoint fast path for tiles whose whole list fits one stage (the common
+// case): the list is staged once, passes A and B run warp-locally over it in
+// list order, and pass B's ballots record, per (warp block, candidate), the
+// mask of pixels where the candidate is a winner. Pass C then walks only the
+// winning (candidate, pixel) pairs, split evenly over the CTA's threads.
 // ---------------------------------------------------------------------------
 
-// Bitonic sort of this warp's candidates by key at (cx, cy); so[] gets the order.
-template <int CH>
-__device__ __forceinline__ void warp_order(int cnt, float cx, float cy, const float4* s_a,
-                                           const float* s_a11, float* sk, short* so) {
-  const int lane = threadIdx.x & 31;
-  int P = 32;
-  while (P < cnt) P <<= 1;
-  for (int i = lane; i < P; i += 32) {
-    float k = F_INF;
-    if (i < cnt) {
-      const float4 a = s_a[i];
-      k = rank_key(cx, cy, a.x, a.y, a.z, a.w, s_a11[i]);
-      if (!(k == k)) k = F_INF;
-    }
-    sk[i] = k;
-    so[i] = (short)i;
-  }
-  __syncwarp();
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = lane; i < P; i += 32) {
-        const int l = i ^ j;
-        if (l > i) {
-          const float a = sk[i], b = sk[l];
-          if ((a > b) == ((i & k) == 0)) {
-            sk[i] = b;
-            sk[l] = a;
-            const short t = so[i];
-            so[i] = so[l];
-            so[l] = t;
-          }
-        }
-      }
-      __syncwarp();
-    }
-  }
-}
-
-// Pass A over the warp's order; `tie` = a tau-valued candidate was dropped.
+// Pass A over the staged list (list order, keys only).
 template <int K>
-__device__ __forceinline__ void fast_keys(int cnt, float px, float py, const float4* s_a,
-                                          const float* s_a11, const short* so, float (&tq)[K],
-                                          bool& tie) {
+__device__ __forceinline__ void staged_keys(int cnt, float px, float py, const float4* s_a,
+                                            const float* s_a11, float (&tq)[K]) {
 #pragma unroll
   for (int k = 0; k < K; ++k) tq[k] = F_INF;
-  float v_drop = F_INF;
-#pragma unroll 2
-  for (int o = 0; o < cnt; ++o) {
-    const int j = so[o];
+#pragma unroll 4
+  for (int j = 0; j < cnt; ++j) {
     const float4 a = s_a[j];
     const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_a11[j]);
-    const float thr = tq[K - 1];
-    const bool better = q < thr;
-    if (q == thr) v_drop = fminf(v_drop, q);  // rejected at the threshold
+    const bool better = q < tq[K - 1];
     if (__any_sync(FULL_MASK, better)) {
       float x = better ? q : F_INF;
 #pragma unroll
@@ -232,77 +183,49 @@ __device__ __forceinline__ void fast_keys(int cnt, float px, float py, const flo
         x = fmaxf(tq[k], x);
         tq[k] = lo;
       }
-      if (better && tq[K - 1] == thr) v_drop = fminf(v_drop, thr);  // evicted at it
     }
   }
-  tie = tq[K - 1] < F_INF && v_drop == tq[K - 1];
 }
 
-// Pass B over the staged list: blend the winners and, if MASK, store the
-// ballot of winning live pixels per candidate in mask_w[] (this warp's row).
-template <int K, int NC, bool MASK>
-__device__ __forceinline__ void fast_blend(const RenderParams& p, int cnt, float px, float py,
-                                           bool live, const float (&tq)[K], bool warp_tie,
-                                           const float4* s_a, const float* s_a11,
-                                           const int* s_gid, const short* so,
-                                           unsigned* mask_w, PixelBlend<Chan<NC>::R>& r) {
+// Pass B over the staged list: exact (q, index) membership, blend, and the
+// ballot of winning live pixels of this warp per candidate into mask_w[].
+template <int K, int NC>
+__device__ __forceinline__ void staged_blend(const RenderParams& p, int cnt, float px, float py,
+                                             bool live, const float (&tq)[K], const float4* s_a,
+                                             const float* s_a11, const int* s_gid,
+                                             unsigned* mask_w, PixelBlend<Chan<NC>::R>& r) {
   constexpr int NCR = Chan<NC>::R;
   const int n = nchan<NC>(p);
   const int lane = threadIdx.x & 31;
   r.q0 = tq[0];
   r.tau = tq[K - 1];
-  r.posK = 0x7fffffff;
+  r.posK = -1;
   r.Z = 0.0f;
 #pragma unroll
   for (int c = 0; c < NCR; ++c) r.cr[c] = 0.0f;
-  if (!warp_tie) {
-    const int need = min(K, cnt);
-    int found = 0;
-    for (int o = 0; o < cnt; ++o) {
-      if (!__any_sync(FULL_MASK, found < need)) break;
-      const int j = so[o];
-      const float4 a = s_a[j];
-      const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_a11[j]);
-      const bool win = found < need && q <= r.tau;
-      const unsigned bal = __ballot_sync(FULL_MASK, win);
-      if (MASK) {
-        const unsigned lb = __ballot_sync(FULL_MASK, win && live);
-        if (lane == 0) mask_w[j] = lb;
-      }
-      if (bal && win) {
-        ++found;
-        const float w = exp2f((r.q0 - q) * HALF_LOG2E);
-        r.Z += w;
-        const float* col = p.color + (int64_t)s_gid[j] * n;
+  int lt = 0;
 #pragma unroll
-        for (int c = 0; c < NCR; ++c)
-          if (NC > 0 || c < n) r.cr[c] = fmaf(w, col[c], r.cr[c]);
-      }
+  for (int k = 0; k < K; ++k) lt += tq[k] < r.tau ? 1 : 0;
+  int eq_left = K - lt;
+#pragma unroll 2
+  for (int j = 0; j < cnt; ++j) {
+    const float4 a = s_a[j];
+    const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_a11[j]);
+    bool win = q < r.tau;
+    if (q == r.tau && eq_left > 0) {
+      win = true;
+      --eq_left;
+      r.posK = j;
     }
-  } else {
-    int lt = 0;
+    const unsigned bal = __ballot_sync(FULL_MASK, win && live);
+    if (lane == 0) mask_w[j] = bal;
+    if (win) {
+      const float w = exp2f((r.q0 - q) * HALF_LOG2E);
+      r.Z += w;
+      const float* col = p.color + (int64_t)s_gid[j] * n;
 #pragma unroll
-    for (int k = 0; k < K; ++k) lt += tq[k] < r.tau ? 1 : 0;
-    int eq_left = K - lt;
-    for (int j = 0; j < cnt; ++j) {
-      const float4 a = s_a[j];
-      const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_a11[j]);
-      bool win = q < r.tau;
-      if (q == r.tau && eq_left > 0) {
-        win = true;
-        --eq_left;
-        r.posK = j;
-      }
-      const unsigned bal = __ballot_sync(FULL_MASK, win && live);
-      if (MASK && lane == 0) mask_w[j] = bal;
-      if (win) {
-        const float w = exp2f((r.q0 - q) * HALF_LOG2E);
-        r.Z += w;
-        const float* col = p.color + (int64_t)s_gid[j] * n;
-#pragma unroll
-        for (int c = 0; c < NCR; ++c)
-          if (NC > 0 || c < n) r.cr[c] = fmaf(w, col[c], r.cr[c]);
-      }
+      for (int c = 0; c < NCR; ++c)
+        if (NC > 0 || c < n) r.cr[c] = fmaf(w, col[c], r.cr[c]);
     }
   }
   const float iz = r.Z > 0.0f ? 1.0f / r.Z : 0.0f;
@@ -310,46 +233,22 @@ __device__ __forceinline__ void fast_blend(const RenderParams& p, int cnt, float
   for (int c = 0; c < NCR; ++c) r.cr[c] *= iz;
 }
 
-template <int TILE>
-__device__ __forceinline__ float2 block_centre(int x0, int y0) {
-  constexpr int BPR = TILE / 8;
-  const int w = threadIdx.x >> 5;
-  return make_float2((float)(x0 + (w % BPR) * 8 + 4), (float)(y0 + (w / BPR) * 4 + 2));
-}
-
 template <int TILE, int K, int NC>
 __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(RenderParams p) {
   constexpr int NT = TILE * TILE;
-  constexpr int NWB = NT / 32;
   __shared__ float4 s_a[NT];
   __shared__ float s_a11[NT];
   __shared__ int s_gid[NT];
-  __shared__ float s_key[NWB][NT];
-  __shared__ short s_ord[NWB][NT];
   const int tile_id = blockIdx.x;
   const int tx = tile_id % p.tiles_x, ty = tile_id / p.tiles_x;
   const int2 lp = pixel_of<TILE>(threadIdx.x);
   const int x = tx * TILE + lp.x, y = ty * TILE + lp.y;
   const float px = (float)x + 0.5f, py = (float)y + 0.5f;
   const int2 range = p.range[tile_id];
-  const int len = range.y - range.x;
   float tq[K];
+  select_keys<TILE, K, NT>(p, range, px, py, tq, s_a, s_a11, s_gid);
   PixelBlend<Chan<NC>::R> r;
-  if (len <= NT) {
-    stage_chunk<NT>(p, range.x, len, s_a, s_a11, s_gid);
-    __syncthreads();
-    const int w = threadIdx.x >> 5;
-    const float2 c = block_centre<TILE>(tx * TILE, ty * TILE);
-    warp_order<NT>(len, c.x, c.y, s_a, s_a11, s_key[w], s_ord[w]);
-    bool tie;
-    fast_keys<K>(len, px, py, s_a, s_a11, s_ord[w], tq, tie);
-    const bool warp_tie = __any_sync(FULL_MASK, tie);
-    fast_blend<K, NC, false>(p, len, px, py, true, tq, warp_tie, s_a, s_a11, s_gid, s_ord[w],
-                             nullptr, r);
-  } else {
-    select_keys<TILE, K, NT>(p, range, px, py, tq, s_a, s_a11, s_gid);
-    blend_pass<TILE, K, NC, NT>(p, range, px, py, tq, r, s_a, s_a11, s_gid);
-  }
+  blend_pass<TILE, K, NC, NT>(p, range, px, py, tq, r, s_a, s_a11, s_gid);
   if (x >= p.W || y >= p.H) return;
   const int n = nchan<NC>(p);
   const int64_t plane = (int64_t)p.H * p.W;
@@ -372,141 +271,234 @@ struct TileCtx {
 // Dynamic shared-memory layout of the adjoint kernel (in 4-byte words), for
 // NT pixels, n channels and CH Gaussians per stage.
 struct BwdSmem {
-  int a, a11, gid, ps0, ps1, gh, part, loss, key, ord, mask, items, inv, hist, total;
+  int a, a11, gid, ps0, ps1, gh, part, slotj, loss, scan, mask, off, total;
 };
 __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   const int NWB = NT / 32;
   BwdSmem L;
   int o = 0;
-  L.a = o;     o += 4 * NT;          // float4 staged geometry
+  L.a = o;     o += 4 * NT;            // float4 staged geometry
   L.a11 = o;   o += NT;
   L.gid = o;   o += NT;
-  L.ps0 = o;   o += 4 * NT;          // float4 (px, py, tau, q0)
-  L.ps1 = o;   o += 2 * NT;          // float2 (posK bits, beta)
-  L.gh = o;    o += n * NT;          // per-pixel -g/(2Z), channel-major
-  L.part = o;  o += (5 + n) * NT;    // pass C partial sums
-  L.loss = o;  o += 2 * (NT / 32);   // doubles
-  L.key = o;   o += NWB * CH;        // per-warp candidate order: keys
-  L.ord = o;   o += (NWB * CH + 1) / 2;  // shorts
-  L.mask = o;  o += NWB * CH;        // winner masks [warp block][candidate]
-  L.items = o; o += NWB * CH;        // (candidate, block) work items
-  L.inv = o;   o += (NWB * CH + 1) / 2;  // shorts: item position of (candidate, block)
-  L.hist = o;  o += 36;
+  L.ps0 = o;   o += 4 * NT;            // float4 (px, py, tau, q0)
+  L.ps1 = o;   o += 2 * NT;            // float2 (posK bits, beta)
+  L.gh = o;    o += n * NT;            // per-pixel -g/(2Z), channel-major
+  L.part = o;  o += 2 * (5 + n) * NT;  // pass C partial sums (two slots per thread)
+  L.slotj = o; o += 2 * NT;            // candidate held by each slot
+  L.loss = o;  o += 2 * (NT / 32) + 2; // doubles
+  L.scan = o;  o += 34;                // integer block-scan scratch
+  L.mask = o;  o += NWB * CH;          // winner masks [warp block][candidate]
+  L.off = o;   o += NWB * CH + 1;      // pair offsets of (candidate, block) items
   L.total = o;
   return L;
 }
 
-// Adjoint pass C of the fast path: visit only the (candidate, warp block)
-// items whose mask is non-empty, longest first so that the lanes of a warp
-// get similar loops; each item's sums go to its own slot and every candidate
-// adds its items' slots in block order (no shared atomics on floats).
+// Converts a candidate's moment sums into parameter gradients and adds them.
+// T = sum over its winning pixels of G*(dx, dy, dx^2, dx dy, dy^2) with
+// G = dL/dq; Tc = sum of w * (-g/(2Z)) per channel.
+template <int NC>
+__device__ __forceinline__ void emit_grad(const RenderParams& p, const TileCtx& t, int gid,
+                                          const float (&T)[5],
+                                          const float (&Tc)[Chan<NC>::R]) {
+  constexpr int NCR = Chan<NC>::R;
+  const int n = nchan<NC>(p);
+  const GRec rc = p.rec[gid];
+  const float2 cs = p.trig[gid];
+  const float A00 = rc.a.z, B = rc.a.w, A11 = rc.b.x, t1 = rc.b.z, t2 = rc.b.w;
+  const float T1 = t1 * t1, T2 = t2 * t2;
+  const float c2 = cs.x * cs.x, s2 = cs.y * cs.y, sc = cs.x * cs.y;
+  // q = A00 dx^2 + B dx dy + A11 dy^2 with d = x - mu_px
+  const float d_mx = -(2.0f * A00 * T[0] + B * T[1]);
+  const float d_my = -(B * T[0] + 2.0f * A11 * T[1]);
+  const float dT1 = T[2] * c2 + T[4] * s2 + 2.0f * T[3] * sc;
+  const float dT2 = T[2] * s2 + T[4] * c2 - 2.0f * T[3] * sc;
+  const float d_th = (T1 - T2) * (2.0f * sc * (T[4] - T[2]) + 2.0f * (c2 - s2) * T[3]);
+  float* gdst = p.grad + (int64_t)gid * (5 + n);
+  atomicAdd(gdst + 0, d_mx * (float)t.W);
+  atomicAdd(gdst + 1, d_my * (float)t.H);
+  atomicAdd(gdst + 2, d_th);
+  atomicAdd(gdst + 3, 2.0f * t1 * dT1);
+  atomicAdd(gdst + 4, 2.0f * t2 * dT2);
+#pragma unroll
+  for (int c = 0; c < NCR; ++c)
+    if (NC > 0 || c < n) atomicAdd(gdst + 5 + c, -2.0f * Tc[c]);  // w g / Z
+}
+
+__device__ __forceinline__ int block_scan_int(int v, int* scratch, int& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(FULL_MASK, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) scratch[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    const int wv = lane < nw ? scratch[lane] : 0;
+    int wi = wv;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(FULL_MASK, wi, o);
+      if (lane >= o) wi += u;
+    }
+    if (lane < nw) scratch[lane] = wi - wv;
+    if (lane == nw - 1) scratch[32] = wi;
+  }
+  __syncthreads();
+  const int r = scratch[warp] + incl - v;
+  total = scratch[32];
+  __syncthreads();
+  return r;
+}
+
+// Pass C of the fast path. The winning (candidate, pixel) pairs, in
+// (candidate, warp block, pixel) order, are split into equal contiguous
+// ranges, one per thread. A thread accumulates the candidates of its range
+// in registers; a candidate whose pairs all lie inside one range is finished
+// by that thread, the first and last candidates of every range go to two
+// slots, and each candidate's owner thread adds up the slots that hold it.
 template <int TILE, int NC, int CH>
-__device__ __forceinline__ void fast_pass_c(const RenderParams& p, const TileCtx& t, int cnt,
+__device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx& t, int cnt,
                                             const float4* s_a, const float* s_a11,
                                             const int* s_gid, const unsigned* s_mask,
                                             const float4* s_ps0, const float2* s_ps1,
-                                            const float* s_gh, float* s_part,
-                                            unsigned* s_items, short* s_inv, int* s_hist) {
+                                            const float* s_gh, float* s_slot, int* s_slotj,
+                                            int* s_off, int* s_scan) {
   constexpr int NT = TILE * TILE;
   constexpr int NWB = NT / 32;
   constexpr int NCR = Chan<NC>::R;
   const int n = nchan<NC>(p);
   const int np = 5 + n;
   const int nit = cnt * NWB;
-  if (threadIdx.x < 36) s_hist[threadIdx.x] = 0;
-  __syncthreads();
-  for (int it = threadIdx.x; it < nit; it += NT) {
-    const int j = it / NWB, wb = it - j * NWB;
-    const int c = __popc(s_mask[wb * CH + j]);
-    if (c) atomicAdd(&s_hist[32 - c], 1);  // bucket 0 holds the fullest items
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int run = 0;
-    for (int b = 0; b < 33; ++b) {
-      const int v = s_hist[b];
-      s_hist[b] = run;
-      run += v;
+  auto mask_of = [&](int it) { return s_mask[(it % NWB) * CH + it / NWB]; };
+  // exclusive offsets of the items' pair counts
+  const int per_it = (nit + NT - 1) / NT;
+  const int i0 = (int)threadIdx.x * per_it;
+  int loc = 0;
+  for (int k = 0; k < per_it; ++k)
+    if (i0 + k < nit) loc += __popc(mask_of(i0 + k));
+  int P;
+  int run = block_scan_int(loc, s_scan, P);
+  for (int k = 0; k < per_it; ++k)
+    if (i0 + k < nit) {
+      s_off[i0 + k] = run;
+      run += __popc(mask_of(i0 + k));
     }
-    s_hist[33] = run;
-  }
-  __syncthreads();
-  const int total = s_hist[33];
-  for (int it = threadIdx.x; it < nit; it += NT) {
-    const int j = it / NWB, wb = it - j * NWB;
-    const int c = __popc(s_mask[wb * CH + j]);
-    short pos = -1;
-    if (c) {
-      const int q = atomicAdd(&s_hist[32 - c], 1);
-      s_items[q] = ((unsigned)j << 8) | (unsigned)wb;
-      pos = (short)q;
-    }
-    s_inv[j * NWB + wb] = pos;
-  }
+  if (threadIdx.x == 0) s_off[nit] = P;
+  s_slotj[2 * threadIdx.x] = -1;
+  s_slotj[2 * threadIdx.x + 1] = -1;
   __syncthreads();
 
-  float T[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  float Tc[NCR];
-#pragma unroll
-  for (int c = 0; c < NCR; ++c) Tc[c] = 0.0f;
-  for (int rb = 0; rb < total; rb += NT) {
-    const int it = rb + (int)threadIdx.x;
-    if (it < total) {
-      const unsigned code = s_items[it];
-      const int j = (int)(code >> 8), wb = (int)(code & 255u);
-      unsigned m = s_mask[wb * CH + j];
-      const float4 a = s_a[j];
-      const float a11 = s_a11[j];
-      const float* col = p.color + (int64_t)s_gid[j] * n;
-      float cc[NCR];
+  const int per = (P + NT - 1) / NT;
+  const int r0 = (int)threadIdx.x * per;
+  const int r1 = min(P, r0 + per);
+  if (r0 < r1) {
+    auto item_of = [&](int e) {  // largest item whose offset is <= e
+      int lo = 0, hi = nit - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_off[mid] <= e) lo = mid; else hi = mid - 1;
+      }
+      return lo;
+    };
+    int it = item_of(r0);
+    const int j_first = it / NWB;
+    const int j_last = item_of(r1 - 1) / NWB;
+    unsigned m = mask_of(it);
+    for (int k = r0 - s_off[it]; k > 0; --k) m &= m - 1;
+    int j = j_first, wb = it - j * NWB;
+    float4 a = s_a[j];
+    float a11 = s_a11[j];
+    float cc[NCR];
+    auto load_colour = [&](int jj) {
+      const float* col = p.color + (int64_t)s_gid[jj] * n;
 #pragma unroll
       for (int c = 0; c < NCR; ++c) cc[c] = (NC > 0 || c < n) ? col[c] : 0.0f;
-      float S1 = 0.f, S2 = 0.f, S11 = 0.f, S12 = 0.f, S22 = 0.f;
-      float Sc[NCR];
+    };
+    load_colour(j);
+    float T[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float Tc[NCR];
 #pragma unroll
-      for (int c = 0; c < NCR; ++c) Sc[c] = 0.0f;
-      while (m) {
-        const int i = wb * 32 + (__ffs(m) - 1);
-        m &= m - 1;
-        const float4 s0 = s_ps0[i];
-        const float beta = s_ps1[i].y;
-        const float dx = __fsub_rn(s0.x, a.x);
-        const float dy = __fsub_rn(s0.y, a.y);
-        const float h = __fmaf_rn(a.w, dy, __fmul_rn(a.z, dx));
-        const float q = __fmaf_rn(h, dx, __fmul_rn(__fmul_rn(a11, dy), dy));
-        const float w = exp2f((s0.w - q) * HALF_LOG2E);
-        float gd = -beta;
+    for (int c = 0; c < NCR; ++c) Tc[c] = 0.0f;
+    auto flush = [&](int jj) {
+      if (jj == j_first || jj == j_last) {
+        const int slot = 2 * (int)threadIdx.x + (jj == j_first ? 0 : 1);
+        float* dst = s_slot + slot * np;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) dst[k] = T[k];
 #pragma unroll
         for (int c = 0; c < NCR; ++c)
-          if (NC > 0 || c < n) gd = fmaf(s_gh[c * NT + i], cc[c], gd);
-        const float Gq = w * gd;
-        const float e1 = Gq * dx, e2 = Gq * dy;
-        S1 += e1;
-        S2 += e2;
-        S11 = fmaf(e1, dx, S11);
-        S12 = fmaf(e1, dy, S12);
-        S22 = fmaf(e2, dy, S22);
-#pragma unroll
-        for (int c = 0; c < NCR; ++c)
-          if (NC > 0 || c < n) Sc[c] = fmaf(w, s_gh[c * NT + i], Sc[c]);
+          if (NC > 0 || c < n) dst[5 + c] = Tc[c];
+        s_slotj[slot] = jj;
+      } else {
+        const int gid = s_gid[jj];
+        if ((unsigned)gid < (unsigned)p.N) emit_grad<NC>(p, t, gid, T, Tc);
       }
-      float* dst = s_part + threadIdx.x * np;
-      dst[0] = S1;
-      dst[1] = S2;
-      dst[2] = S11;
-      dst[3] = S12;
-      dst[4] = S22;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) T[k] = 0.0f;
+#pragma unroll
+      for (int c = 0; c < NCR; ++c) Tc[c] = 0.0f;
+    };
+    for (int e = r0; e < r1; ++e) {
+      const int i = wb * 32 + (__ffs(m) - 1);
+      m &= m - 1;
+      const float4 s0 = s_ps0[i];
+      const float beta = s_ps1[i].y;
+      // the ranking key of pass A, recomputed bit for bit (same sequence)
+      const float dx = __fsub_rn(s0.x, a.x);
+      const float dy = __fsub_rn(s0.y, a.y);
+      const float h = __fmaf_rn(a.w, dy, __fmul_rn(a.z, dx));
+      const float q = __fmaf_rn(h, dx, __fmul_rn(__fmul_rn(a11, dy), dy));
+      const float w = exp2f((s0.w - q) * HALF_LOG2E);
+      float gd = -beta;
 #pragma unroll
       for (int c = 0; c < NCR; ++c)
-        if (NC > 0 || c < n) dst[5 + c] = Sc[c];
+        if (NC > 0 || c < n) gd = fmaf(s_gh[c * NT + i], cc[c], gd);
+      const float Gq = w * gd;
+      const float e1 = Gq * dx, e2 = Gq * dy;
+      T[0] += e1;
+      T[1] += e2;
+      T[2] = fmaf(e1, dx, T[2]);
+      T[3] = fmaf(e1, dy, T[3]);
+      T[4] = fmaf(e2, dy, T[4]);
+#pragma unroll
+      for (int c = 0; c < NCR; ++c)
+        if (NC > 0 || c < n) Tc[c] = fmaf(w, s_gh[c * NT + i], Tc[c]);
+      if (m == 0 && e + 1 < r1) {
+        do {
+          ++it;
+          m = mask_of(it);
+        } while (m == 0);
+        const int nj = it / NWB;
+        wb = it - nj * NWB;
+        if (nj != j) {
+          flush(j);
+          j = nj;
+          a = s_a[j];
+          a11 = s_a11[j];
+          load_colour(j);
+        }
+      }
     }
-    __syncthreads();
-    if ((int)threadIdx.x < cnt) {
-      const int j = threadIdx.x;
-      for (int wb = 0; wb < NWB; ++wb) {
-        const int pos = s_inv[j * NWB + wb];
-        if (pos >= rb && pos < rb + NT) {
-          const float* src = s_part + (pos - rb) * np;
+    flush(j);
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < cnt) {
+    const int j = threadIdx.x;
+    const int e0 = s_off[j * NWB], e1 = s_off[(j + 1) * NWB];
+    if (e1 > e0) {
+      float T[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      float Tc[NCR];
+#pragma unroll
+      for (int c = 0; c < NCR; ++c) Tc[c] = 0.0f;
+      bool held = false;
+      for (int th = e0 / per; th <= (e1 - 1) / per; ++th) {
+        for (int sl = 0; sl < 2; ++sl) {
+          if (s_slotj[2 * th + sl] != j) continue;
+          held = true;
+          const float* src = s_slot + (2 * th + sl) * np;
 #pragma unroll
           for (int k = 0; k < 5; ++k) T[k] += src[k];
 #pragma unroll
@@ -514,33 +506,8 @@ __device__ __forceinline__ void fast_pass_c(const RenderParams& p, const TileCtx
             if (NC > 0 || c < n) Tc[c] += src[5 + c];
         }
       }
-    }
-    __syncthreads();
-  }
-  if ((int)threadIdx.x < cnt) {
-    const int gid = s_gid[threadIdx.x];
-    bool any = false;
-    for (int wb = 0; wb < NWB; ++wb) any |= s_inv[threadIdx.x * NWB + wb] >= 0;
-    if (any && (unsigned)gid < (unsigned)p.N) {
-      const GRec rc = p.rec[gid];
-      const float2 cs = p.trig[gid];
-      const float A00 = rc.a.z, B = rc.a.w, A11 = rc.b.x, t1 = rc.b.z, t2 = rc.b.w;
-      const float T1 = t1 * t1, T2 = t2 * t2;
-      const float c2 = cs.x * cs.x, s2 = cs.y * cs.y, sc = cs.x * cs.y;
-      const float d_mx = -(2.0f * A00 * T[0] + B * T[1]);
-      const float d_my = -(B * T[0] + 2.0f * A11 * T[1]);
-      const float dT1 = T[2] * c2 + T[4] * s2 + 2.0f * T[3] * sc;
-      const float dT2 = T[2] * s2 + T[4] * c2 - 2.0f * T[3] * sc;
-      const float d_th = (T1 - T2) * (2.0f * sc * (T[4] - T[2]) + 2.0f * (c2 - s2) * T[3]);
-      float* gdst = p.grad + (int64_t)gid * np;
-      atomicAdd(gdst + 0, d_mx * (float)t.W);
-      atomicAdd(gdst + 1, d_my * (float)t.H);
-      atomicAdd(gdst + 2, d_th);
-      atomicAdd(gdst + 3, 2.0f * t1 * dT1);
-      atomicAdd(gdst + 4, 2.0f * t2 * dT2);
-#pragma unroll
-      for (int c = 0; c < NCR; ++c)
-        if (NC > 0 || c < n) atomicAdd(gdst + 5 + c, -2.0f * Tc[c]);
+      const int gid = s_gid[j];
+      if (held && (unsigned)gid < (unsigned)p.N) emit_grad<NC>(p, t, gid, T, Tc);
     }
   }
 }
@@ -561,12 +528,9 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   float* s_gh = smem + SL.gh;
   float* s_part = smem + SL.part;
   double* s_loss = reinterpret_cast<double*>(smem + SL.loss);
-  float* s_key = smem + SL.key;
-  short* s_ord = reinterpret_cast<short*>(smem + SL.ord);
   unsigned* s_mask = reinterpret_cast<unsigned*>(smem + SL.mask);
-  unsigned* s_items = reinterpret_cast<unsigned*>(smem + SL.items);
-  short* s_inv = reinterpret_cast<short*>(smem + SL.inv);
-  int* s_hist = reinterpret_cast<int*>(smem + SL.hist);
+  int* s_off = reinterpret_cast<int*>(smem + SL.off);
+  int* s_slotj = reinterpret_cast<int*>(smem + SL.slotj);
 
   const int2 lp = pixel_of<TILE>(threadIdx.x);
   const int x = t.x0 + lp.x, y = t.y0 + lp.y;
@@ -581,16 +545,11 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   if (fast) {
     __syncthreads();  // the previous tile of a persistent CTA is done with smem
     stage_chunk<CH>(p, range.x, len, s_a, s_a11, s_gid);
-    for (int i = threadIdx.x; i < NWB * CH; i += NT) s_mask[i] = 0u;
     __syncthreads();
     const int w = threadIdx.x >> 5;
-    const float2 c = block_centre<TILE>(t.x0, t.y0);
-    warp_order<CH>(len, c.x, c.y, s_a, s_a11, s_key + w * CH, s_ord + w * CH);
-    bool tie;
-    fast_keys<K>(len, px, py, s_a, s_a11, s_ord + w * CH, tq, tie);
-    const bool warp_tie = __any_sync(FULL_MASK, tie);
-    fast_blend<K, NC, true>(p, len, px, py, x < t.W && y < t.H, tq, warp_tie, s_a, s_a11, s_gid,
-                            s_ord + w * CH, s_mask + w * CH, r);
+    staged_keys<K>(len, px, py, s_a, s_a11, tq);
+    staged_blend<K, NC>(p, len, px, py, x < t.W && y < t.H, tq, s_a, s_a11, s_gid,
+                        s_mask + w * CH, r);
   } else {
     select_keys<TILE, K, CH>(p, range, px, py, tq, s_a, s_a11, s_gid);
     blend_pass<TILE, K, NC, CH>(p, range, px, py, tq, r, s_a, s_a11, s_gid);
@@ -635,8 +594,8 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
 
   // ---- pass C: candidate-major accumulation of the adjoint
   if (fast) {
-    fast_pass_c<TILE, NC, CH>(p, t, len, s_a, s_a11, s_gid, s_mask, s_ps0, s_ps1, s_gh, s_part,
-                              s_items, s_inv, s_hist);
+    flat_pass_c<TILE, NC, CH>(p, t, len, s_a, s_a11, s_gid, s_mask, s_ps0, s_ps1, s_gh, s_part,
+                              s_slotj, s_off, reinterpret_cast<int*>(smem + SL.scan));
     return;
   }
   const int np = 5 + n;
