@@ -95,6 +95,15 @@ __device__ __forceinline__ void topk_insert(float (&tq)[K], int (&tid)[K], float
   }
 }
 
+// Blend weight exp(-(q - q_min)/2) = 2^((q_min - q) log2(e)/2) on the special
+// function unit (ex2.approx, relative error a few 2^-23; 2^0 is exactly 1;
+// weights below 2^-126 flush to zero, where they are negligible in the blend).
+__device__ __forceinline__ float blend_weight(float q0, float q) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"((q0 - q) * HALF_LOG2E));
+  return y;
+}
+
 __device__ __forceinline__ float sign_f(float x) {
   return x > 0.0f ? 1.0f : (x < 0.0f ? -1.0f : 0.0f);
 }

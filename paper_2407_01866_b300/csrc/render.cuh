@@ -45,9 +45,12 @@ __device__ __forceinline__ int2 pixel_of(int t) {
 constexpr float F_INF = __builtin_huge_valf();
 
 // Stage list entries [base, base+cnt) of the tile: geometry and index.
-template <int NT>
+// Colours of staged candidates live in shared memory, channel-major
+// s_col[c * NT + j], when the channel count is a compile-time constant.
+template <int NT, int NC>
 __device__ __forceinline__ void stage_chunk(const RenderParams& p, int base, int cnt,
-                                            float4* s_a, float* s_a11, int* s_gid) {
+                                            float4* s_a, float* s_a11, int* s_gid,
+                                            float* s_col) {
   if ((int)threadIdx.x < cnt) {
     const int gid = p.list[base + threadIdx.x];
     if ((unsigned)gid < (unsigned)p.N) {
@@ -55,13 +58,30 @@ __device__ __forceinline__ void stage_chunk(const RenderParams& p, int base, int
       s_a[threadIdx.x] = g.a;
       s_a11[threadIdx.x] = g.b.x;
       s_gid[threadIdx.x] = gid;
+      if (NC > 0) {
+#pragma unroll
+        for (int c = 0; c < (NC > 0 ? NC : 1); ++c)
+          s_col[c * NT + threadIdx.x] = p.color[(int64_t)gid * NC + c];
+      }
     } else {  // corrupt list entry: a NaN key is never selected
       s_a[threadIdx.x] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
       s_a11[threadIdx.x] = 0.0f;
       s_gid[threadIdx.x] = -1;
+      if (NC > 0) {
+#pragma unroll
+        for (int c = 0; c < (NC > 0 ? NC : 1); ++c) s_col[c * NT + threadIdx.x] = 0.0f;
+      }
       atomicOr(&p.status->flags, FLAG_INTERNAL);
     }
   }
+}
+
+// Channel c of staged candidate j (shared memory if staged, else global).
+template <int NT, int NC>
+__device__ __forceinline__ float staged_colour(const RenderParams& p, const float* s_col,
+                                               const int* s_gid, int j, int c) {
+  if (NC > 0) return s_col[c * NT + j];
+  return p.color[(int64_t)s_gid[j] * p.n + c];
 }
 
 // Pass A: the K smallest keys at (px, py), ascending. CH list entries are
@@ -75,7 +95,7 @@ __device__ __forceinline__ void select_keys(const RenderParams& p, int2 range, f
   for (int base = range.x; base < range.y; base += CH) {
     const int cnt = min(CH, range.y - base);
     __syncthreads();
-    stage_chunk<CH>(p, base, cnt, s_a, s_a11, s_gid);
+    stage_chunk<CH, 0>(p, base, cnt, s_a, s_a11, s_gid, nullptr);
     __syncthreads();
 #pragma unroll 4
     for (int j = 0; j < cnt; ++j) {
@@ -110,7 +130,7 @@ template <int TILE, int K, int NC, int CH>
 __device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, float px,
                                            float py, const float (&tq)[K],
                                            PixelBlend<Chan<NC>::R>& r, float4* s_a,
-                                           float* s_a11, int* s_gid) {
+                                           float* s_a11, int* s_gid, float* s_col) {
   constexpr int NCR = Chan<NC>::R;
   const int n = nchan<NC>(p);
   r.q0 = tq[0];
@@ -126,7 +146,7 @@ __device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, fl
   for (int base = range.x; base < range.y; base += CH) {
     const int cnt = min(CH, range.y - base);
     __syncthreads();
-    stage_chunk<CH>(p, base, cnt, s_a, s_a11, s_gid);
+    stage_chunk<CH, NC>(p, base, cnt, s_a, s_a11, s_gid, s_col);
     __syncthreads();
     const int rel = base - range.x;
 #pragma unroll 2
@@ -141,12 +161,12 @@ __device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, fl
       }
       if (__any_sync(FULL_MASK, win)) {
         if (win) {
-          const float w = exp2f((r.q0 - q) * HALF_LOG2E);  // exactly 1 at q = q_min
+          const float w = blend_weight(r.q0, q);  // exactly 1 at q = q_min
           r.Z += w;
-          const float* col = p.color + (int64_t)s_gid[j] * n;
 #pragma unroll
           for (int c = 0; c < NCR; ++c)
-            if (NC > 0 || c < n) r.cr[c] = fmaf(w, col[c], r.cr[c]);
+            if (NC > 0 || c < n)
+              r.cr[c] = fmaf(w, staged_colour<CH, NC>(p, s_col, s_gid, j, c), r.cr[c]);
         }
       }
     }
@@ -189,11 +209,12 @@ __device__ __forceinline__ void staged_keys(int cnt, float px, float py, const f
 
 // Pass B over the staged list: exact (q, index) membership, blend, and the
 // ballot of winning live pixels of this warp per candidate into mask_w[].
-template <int K, int NC>
+template <int K, int NC, int CH>
 __device__ __forceinline__ void staged_blend(const RenderParams& p, int cnt, float px, float py,
                                              bool live, const float (&tq)[K], const float4* s_a,
                                              const float* s_a11, const int* s_gid,
-                                             unsigned* mask_w, PixelBlend<Chan<NC>::R>& r) {
+                                             const float* s_col, unsigned* mask_w,
+                                             PixelBlend<Chan<NC>::R>& r) {
   constexpr int NCR = Chan<NC>::R;
   const int n = nchan<NC>(p);
   const int lane = threadIdx.x & 31;
@@ -220,12 +241,12 @@ __device__ __forceinline__ void staged_blend(const RenderParams& p, int cnt, flo
     const unsigned bal = __ballot_sync(FULL_MASK, win && live);
     if (lane == 0) mask_w[j] = bal;
     if (win) {
-      const float w = exp2f((r.q0 - q) * HALF_LOG2E);
+      const float w = blend_weight(r.q0, q);
       r.Z += w;
-      const float* col = p.color + (int64_t)s_gid[j] * n;
 #pragma unroll
       for (int c = 0; c < NCR; ++c)
-        if (NC > 0 || c < n) r.cr[c] = fmaf(w, col[c], r.cr[c]);
+        if (NC > 0 || c < n)
+          r.cr[c] = fmaf(w, staged_colour<CH, NC>(p, s_col, s_gid, j, c), r.cr[c]);
     }
   }
   const float iz = r.Z > 0.0f ? 1.0f / r.Z : 0.0f;
@@ -239,6 +260,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(RenderParams p) {
   __shared__ float4 s_a[NT];
   __shared__ float s_a11[NT];
   __shared__ int s_gid[NT];
+  __shared__ float s_col[NT * (NC > 0 ? NC : 1)];
   const int tile_id = blockIdx.x;
   const int tx = tile_id % p.tiles_x, ty = tile_id / p.tiles_x;
   const int2 lp = pixel_of<TILE>(threadIdx.x);
@@ -248,7 +270,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(RenderParams p) {
   float tq[K];
   select_keys<TILE, K, NT>(p, range, px, py, tq, s_a, s_a11, s_gid);
   PixelBlend<Chan<NC>::R> r;
-  blend_pass<TILE, K, NC, NT>(p, range, px, py, tq, r, s_a, s_a11, s_gid);
+  blend_pass<TILE, K, NC, NT>(p, range, px, py, tq, r, s_a, s_a11, s_gid, s_col);
   if (x >= p.W || y >= p.H) return;
   const int n = nchan<NC>(p);
   const int64_t plane = (int64_t)p.H * p.W;
@@ -271,7 +293,7 @@ struct TileCtx {
 // Dynamic shared-memory layout of the adjoint kernel (in 4-byte words), for
 // NT pixels, n channels and CH Gaussians per stage.
 struct BwdSmem {
-  int a, a11, gid, ps0, ps1, gh, part, slotj, loss, scan, mask, off, total;
+  int a, a11, gid, col, ps0, ps1, gh, part, slotj, loss, scan, mask, off, total;
 };
 __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   const int NWB = NT / 32;
@@ -280,6 +302,7 @@ __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   L.a = o;     o += 4 * NT;            // float4 staged geometry
   L.a11 = o;   o += NT;
   L.gid = o;   o += NT;
+  L.col = o;   o += n * CH;            // staged colours, channel-major
   L.ps0 = o;   o += 4 * NT;            // float4 (px, py, tau, q0)
   L.ps1 = o;   o += 2 * NT;            // float2 (posK bits, beta)
   L.gh = o;    o += n * NT;            // per-pixel -g/(2Z), channel-major
@@ -362,10 +385,11 @@ __device__ __forceinline__ int block_scan_int(int v, int* scratch, int& total) {
 template <int TILE, int NC, int CH>
 __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx& t, int cnt,
                                             const float4* s_a, const float* s_a11,
-                                            const int* s_gid, const unsigned* s_mask,
-                                            const float4* s_ps0, const float2* s_ps1,
-                                            const float* s_gh, float* s_slot, int* s_slotj,
-                                            int* s_off, int* s_scan) {
+                                            const int* s_gid, const float* s_col,
+                                            const unsigned* s_mask, const float4* s_ps0,
+                                            const float2* s_ps1, const float* s_gh,
+                                            float* s_slot, int* s_slotj, int* s_off,
+                                            int* s_scan) {
   constexpr int NT = TILE * TILE;
   constexpr int NWB = NT / 32;
   constexpr int NCR = Chan<NC>::R;
@@ -413,9 +437,9 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
     float a11 = s_a11[j];
     float cc[NCR];
     auto load_colour = [&](int jj) {
-      const float* col = p.color + (int64_t)s_gid[jj] * n;
 #pragma unroll
-      for (int c = 0; c < NCR; ++c) cc[c] = (NC > 0 || c < n) ? col[c] : 0.0f;
+      for (int c = 0; c < NCR; ++c)
+        cc[c] = (NC > 0 || c < n) ? staged_colour<CH, NC>(p, s_col, s_gid, jj, c) : 0.0f;
     };
     load_colour(j);
     float T[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -451,7 +475,7 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
       const float dy = __fsub_rn(s0.y, a.y);
       const float h = __fmaf_rn(a.w, dy, __fmul_rn(a.z, dx));
       const float q = __fmaf_rn(h, dx, __fmul_rn(__fmul_rn(a11, dy), dy));
-      const float w = exp2f((s0.w - q) * HALF_LOG2E);
+      const float w = blend_weight(s0.w, q);
       float gd = -beta;
 #pragma unroll
       for (int c = 0; c < NCR; ++c)
@@ -523,6 +547,7 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   float4* s_a = reinterpret_cast<float4*>(smem + SL.a);
   float* s_a11 = smem + SL.a11;
   int* s_gid = reinterpret_cast<int*>(smem + SL.gid);
+  float* s_col = smem + SL.col;
   float4* s_ps0 = reinterpret_cast<float4*>(smem + SL.ps0);
   float2* s_ps1 = reinterpret_cast<float2*>(smem + SL.ps1);
   float* s_gh = smem + SL.gh;
@@ -544,15 +569,15 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   PixelBlend<NCR> r;
   if (fast) {
     __syncthreads();  // the previous tile of a persistent CTA is done with smem
-    stage_chunk<CH>(p, range.x, len, s_a, s_a11, s_gid);
+    stage_chunk<CH, NC>(p, range.x, len, s_a, s_a11, s_gid, s_col);
     __syncthreads();
     const int w = threadIdx.x >> 5;
     staged_keys<K>(len, px, py, s_a, s_a11, tq);
-    staged_blend<K, NC>(p, len, px, py, x < t.W && y < t.H, tq, s_a, s_a11, s_gid,
-                        s_mask + w * CH, r);
+    staged_blend<K, NC, CH>(p, len, px, py, x < t.W && y < t.H, tq, s_a, s_a11, s_gid, s_col,
+                            s_mask + w * CH, r);
   } else {
     select_keys<TILE, K, CH>(p, range, px, py, tq, s_a, s_a11, s_gid);
-    blend_pass<TILE, K, NC, CH>(p, range, px, py, tq, r, s_a, s_a11, s_gid);
+    blend_pass<TILE, K, NC, CH>(p, range, px, py, tq, r, s_a, s_a11, s_gid, s_col);
   }
 
   float loss = 0.0f;
@@ -594,7 +619,8 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
 
   // ---- pass C: candidate-major accumulation of the adjoint
   if (fast) {
-    flat_pass_c<TILE, NC, CH>(p, t, len, s_a, s_a11, s_gid, s_mask, s_ps0, s_ps1, s_gh, s_part,
+    flat_pass_c<TILE, NC, CH>(p, t, len, s_a, s_a11, s_gid, s_col, s_mask, s_ps0, s_ps1, s_gh,
+                              s_part,
                               s_slotj, s_off, reinterpret_cast<int*>(smem + SL.scan));
     return;
   }
@@ -629,7 +655,7 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
         const float q = __fmaf_rn(h, dx, __fmul_rn(__fmul_rn(rc.b.x, dy), dy));
         const bool win = q < s0.z || (q == s0.z && pos <= __float_as_int(s1.x));
         if (win) {
-          const float w = exp2f((s0.w - q) * HALF_LOG2E);
+          const float w = blend_weight(s0.w, q);
           float gd = -s1.y;
 #pragma unroll
           for (int c = 0; c < NCR; ++c)
@@ -784,7 +810,7 @@ __global__ void __launch_bounds__(256) k_decode(RenderParams p) {
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     if (tp[k] >= 0) {
-      const float w = exp2f((tq[0] - tq[k]) * HALF_LOG2E);
+      const float w = blend_weight(tq[0], tq[k]);
       Z += w;
       const float* col = p.color + (int64_t)tp[k] * n;
 #pragma unroll
