@@ -37,15 +37,6 @@ static int cuda_fail(cudaError_t e, const char* where) {
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-static int bits_for(int64_t x) {  // bits needed to represent values 0..x
-  int b = 0;
-  while (x > 0) {
-    ++b;
-    x >>= 1;
-  }
-  return b;
-}
-
 WsLayout ws_layout(int64_t N, int n, int H, int W, int tile, int64_t m_cap) {
   WsLayout L = ws_layout_tiles(N, n, (int64_t)((W + tile - 1) / tile) * ((H + tile - 1) / tile),
                                m_cap);
@@ -57,11 +48,7 @@ WsLayout ws_layout(int64_t N, int n, int H, int W, int tile, int64_t m_cap) {
 WsLayout ws_layout_tiles(int64_t N, int n, int64_t T, int64_t m_cap) {
   WsLayout L;
   L.tiles_x = L.tiles_y = 0;
-  L.passes = T <= 1 ? 0 : (bits_for(T - 1) + RADIX_BITS - 1) / RADIX_BITS;
-  L.hist_blocks = m_cap > 0 ? (m_cap + RADIX_ITEMS - 1) / RADIX_ITEMS : 1;
-  const int64_t pn = (N + SCAN_ITEMS - 1) / SCAN_ITEMS;
-  const int64_t ph = (L.hist_blocks * RADIX_DIGITS + SCAN_ITEMS - 1) / SCAN_ITEMS;
-  L.part_len = std::max<int64_t>(1, std::max(pn, ph));
+  L.part_len = std::max<int64_t>(1, (T + SCAN_ITEMS - 1) / SCAN_ITEMS);
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t at = o;
@@ -72,14 +59,12 @@ WsLayout ws_layout_tiles(int64_t N, int n, int64_t T, int64_t m_cap) {
   L.rec = take(sizeof(GRec) * (size_t)N);
   L.trig = take(sizeof(float2) * (size_t)N);
   L.color = take(sizeof(float) * (size_t)N * n);
-  L.cnt = take(sizeof(unsigned int) * (size_t)N);
-  L.off = take(sizeof(unsigned long long) * (size_t)N);
+  L.tcnt = take(sizeof(unsigned int) * (size_t)T);
+  L.toff = take(sizeof(unsigned long long) * (size_t)T);
   L.part = take(sizeof(unsigned long long) * (size_t)L.part_len);
-  L.keys0 = take(sizeof(unsigned int) * (size_t)m_cap);
-  L.keys1 = take(sizeof(unsigned int) * (size_t)m_cap);
-  L.vals0 = take(sizeof(unsigned int) * (size_t)m_cap);
-  L.vals1 = take(sizeof(unsigned int) * (size_t)m_cap);
-  L.hist = take(sizeof(unsigned int) * (size_t)L.hist_blocks * RADIX_DIGITS);
+  L.vals = take(sizeof(unsigned int) * (size_t)m_cap);
+  L.tmp = take(sizeof(unsigned int) * (size_t)m_cap);
+  L.big = take(sizeof(int) * (size_t)T);
   L.range = take(sizeof(int2) * (size_t)T);
   L.total = o;
   return L;
@@ -238,29 +223,17 @@ int igs_preprocess_bin(const igs_gaussians* g, int32_t H, int32_t W, const igs_c
   p.rec = reinterpret_cast<GRec*>(base + L.rec);
   p.trig = reinterpret_cast<float2*>(base + L.trig);
   p.color_out = reinterpret_cast<float*>(base + L.color);
-  p.cnt = reinterpret_cast<unsigned int*>(base + L.cnt);
-  p.off = reinterpret_cast<unsigned long long*>(base + L.off);
-  p.keys = reinterpret_cast<unsigned int*>(base + L.keys0);
-  p.vals = reinterpret_cast<unsigned int*>(base + L.vals0);
+  p.tcnt = reinterpret_cast<unsigned int*>(base + L.tcnt);
+  p.toff = reinterpret_cast<unsigned long long*>(base + L.toff);
+  p.vals = reinterpret_cast<unsigned int*>(base + L.vals);
+  p.tmp = reinterpret_cast<unsigned int*>(base + L.tmp);
+  p.big = reinterpret_cast<int*>(base + L.big);
   p.m_cap = m_capacity;
   p.status = status;
   unsigned long long* part = reinterpret_cast<unsigned long long*>(base + L.part);
-
-  IGS_CUDA(launch_preprocess(p, g->dtype, s), "preprocess");
-  IGS_CUDA(launch_scan_u32_to_u64(p.cnt, p.off, g->N, part, &status->m_needed, s), "scan");
-  IGS_CUDA(launch_emit(p, s), "emit");
-  unsigned int *keys = nullptr, *vals = nullptr;
-  IGS_CUDA(launch_radix_sort(reinterpret_cast<unsigned int*>(base + L.keys0),
-                             reinterpret_cast<unsigned int*>(base + L.vals0),
-                             reinterpret_cast<unsigned int*>(base + L.keys1),
-                             reinterpret_cast<unsigned int*>(base + L.vals1),
-                             reinterpret_cast<unsigned int*>(base + L.hist), part,
-                             L.hist_blocks, L.passes, m_capacity, status, s, &keys, &vals),
-           "sort");
   int2* range = reinterpret_cast<int2*>(base + L.range);
-  IGS_CUDA(launch_ranges(keys, range, L.tiles_x * L.tiles_y, m_capacity, H, W, cfg->tile,
-                         L.tiles_x, status, s),
-           "ranges");
+  IGS_CUDA(run_binning(p, g->dtype, L.tiles_x * L.tiles_y, part, range, s), "binning");
+  const unsigned int* vals = p.vals;
 
   out->H = H;
   out->W = W;

@@ -130,33 +130,23 @@ int batch_bin(const igs_fit_state* st, const BatchGeom& G, const igs_config* cfg
   p.rec = reinterpret_cast<GRec*>(base + L.rec);
   p.trig = reinterpret_cast<float2*>(base + L.trig);
   p.color_out = reinterpret_cast<float*>(base + L.color);
-  p.cnt = reinterpret_cast<unsigned int*>(base + L.cnt);
-  p.off = reinterpret_cast<unsigned long long*>(base + L.off);
-  p.keys = reinterpret_cast<unsigned int*>(base + L.keys0);
-  p.vals = reinterpret_cast<unsigned int*>(base + L.vals0);
+  p.tcnt = reinterpret_cast<unsigned int*>(base + L.tcnt);
+  p.toff = reinterpret_cast<unsigned long long*>(base + L.toff);
+  p.vals = reinterpret_cast<unsigned int*>(base + L.vals);
+  p.tmp = reinterpret_cast<unsigned int*>(base + L.tmp);
+  p.big = reinterpret_cast<int*>(base + L.big);
   p.m_cap = m_cap;
   p.status = status;
   p.img_of = reinterpret_cast<const int*>(base + G.img_of);
   p.img_dims = reinterpret_cast<const int4*>(base + G.dims);
   p.tile_off = reinterpret_cast<const int*>(base + G.tile_off);
   unsigned long long* part = reinterpret_cast<unsigned long long*>(base + L.part);
-  BCUDA(launch_preprocess(p, IGS_F32, s), "batch: preprocess");
-  BCUDA(launch_scan_u32_to_u64(p.cnt, p.off, G.Ntot, part, &status->m_needed, s), "batch: scan");
-  BCUDA(launch_emit(p, s), "batch: emit");
-  unsigned int *keys = nullptr, *vals = nullptr;
-  BCUDA(launch_radix_sort(reinterpret_cast<unsigned int*>(base + L.keys0),
-                          reinterpret_cast<unsigned int*>(base + L.vals0),
-                          reinterpret_cast<unsigned int*>(base + L.keys1),
-                          reinterpret_cast<unsigned int*>(base + L.vals1),
-                          reinterpret_cast<unsigned int*>(base + L.hist), part, L.hist_blocks,
-                          L.passes, m_cap, status, s, &keys, &vals),
-        "batch: sort");
   int2* range = reinterpret_cast<int2*>(base + L.range);
-  BCUDA(launch_ranges(keys, range, (int)G.T, m_cap, 0, 0, BATCH_TILE, 0, status, s),
-        "batch: ranges");
+  BCUDA(run_binning(p, IGS_F32, (int)G.T, part, range, s), "batch: binning");
   BCUDA(launch_tile_evals_batch(range, (int)G.T, p.img_dims, p.tile_off, G.B, BATCH_TILE,
                                 status, s),
         "batch: evals");
+  const unsigned int* vals = p.vals;
   memset(rp, 0, sizeof(*rp));
   rp->range = range;
   rp->list = reinterpret_cast<const int*>(vals);

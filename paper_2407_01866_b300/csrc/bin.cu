@@ -3,14 +3,16 @@
 //
 // Pipeline (all stream-ordered, no host synchronisation, graph-capturable):
 //   k_preprocess   one thread per Gaussian: mu in pixels, inverse covariance
-//                  (Eq. 2), radius 3*max(s), exact count of hit tiles
-//   scan           exclusive prefix sum of the counts -> write offsets, M
-//   k_emit         (tile, gaussian) pairs in Gaussian order
-//   radix sort     stable LSD sort by tile id (8-bit digits): within a tile
-//                  the Gaussians stay in ascending index order, which is the
-//                  tie-break order of the top-K ranking
-//   k_ranges       [start, end) of every tile in the sorted list
-//   k_tile_evals   sum over tiles of |S_j| * pixels(j)
+//                  (Eq. 2), radius 3*max(s); every exact tile hit increments
+//                  that tile's counter
+//   scan           exclusive prefix sum of the tile counters -> list offsets, M
+//   k_emit         every hit takes a slot of its tile's segment (atomic cursor)
+//   k_segsort      one warp per tile sorts its segment by Gaussian index
+//                  (ascending index is the tie-break order of the top-K
+//                  ranking); segments longer than one warp's shared-memory
+//                  window are sorted by whole CTAs in k_segsort_big
+//   k_ranges       [start, end) of every tile from the offsets, and the sum
+//                  over tiles of |S_j| * pixels(j)
 #include <algorithm>
 
 #include "internal.h"
@@ -73,7 +75,6 @@ __global__ void __launch_bounds__(256) k_preprocess(PrepParams p) {
   float A00, B, A11;
   conic_from(c, s, t1, t2, A00, B, A11);
   float r = __fdiv_rn(3.0f, fminf(t1, t2));
-  unsigned int count = 0;
   if (ok && isfinite(mx) && isfinite(my) && isfinite(r)) {
     int x0, x1, y0, y1;
     tile_span(mx, r, p.tile, ig.tiles_x, x0, x1);
@@ -83,7 +84,8 @@ __global__ void __launch_bounds__(256) k_preprocess(PrepParams p) {
       const float Y0 = (float)(ty * p.tile), Y1 = (float)min((ty + 1) * p.tile, ig.H);
       for (int tx = x0; tx <= x1; ++tx) {
         const float X0 = (float)(tx * p.tile), X1 = (float)min((tx + 1) * p.tile, ig.W);
-        count += circle_hits_rect(mx, my, r2, X0, X1, Y0, Y1) ? 1u : 0u;
+        if (circle_hits_rect(mx, my, r2, X0, X1, Y0, Y1))
+          atomicAdd(p.tcnt + ig.tile_base + ty * ig.tiles_x + tx, 1u);
       }
     }
   } else {
@@ -94,7 +96,6 @@ __global__ void __launch_bounds__(256) k_preprocess(PrepParams p) {
   g.b = make_float4(A11, r, t1, t2);
   p.rec[i] = g;
   p.trig[i] = make_float2(c, s);
-  p.cnt[i] = count;
 }
 
 template <bool BATCH>
@@ -107,7 +108,6 @@ __global__ void __launch_bounds__(256) k_emit(PrepParams p) {
   const GRec g = p.rec[i];
   const float mx = g.a.x, my = g.a.y, r = g.b.y;
   if (!(r >= 0.0f) || !isfinite(mx) || !isfinite(my) || !isfinite(r)) return;
-  unsigned long long pos = p.off[i];
   int x0, x1, y0, y1;
   tile_span(mx, r, p.tile, ig.tiles_x, x0, x1);
   tile_span(my, r, p.tile, ig.tiles_y, y0, y1);
@@ -118,11 +118,10 @@ __global__ void __launch_bounds__(256) k_emit(PrepParams p) {
     for (int tx = x0; tx <= x1; ++tx) {
       const float X0 = (float)(tx * p.tile), X1 = (float)min((tx + 1) * p.tile, ig.W);
       if (circle_hits_rect(mx, my, r2, X0, X1, Y0, Y1)) {
-        if (pos < cap) {
-          p.keys[pos] = (unsigned int)(ig.tile_base + ty * ig.tiles_x + tx);
-          p.vals[pos] = (unsigned int)i;
-        }
-        ++pos;
+        const int t = ig.tile_base + ty * ig.tiles_x + tx;
+        // the counter runs back down from the tile's count: one slot per hit
+        const unsigned long long pos = p.toff[t] + (atomicSub(p.tcnt + t, 1u) - 1u);
+        if (pos < cap) p.vals[pos] = (unsigned int)i;
       }
     }
   }
@@ -229,102 +228,155 @@ cudaError_t scan_exclusive(const In* in, Out* out, int64_t n, unsigned long long
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- radix sort
+// ---------------------------------------------------------------- segment sort
 
 __device__ __forceinline__ int64_t live_items(const DevStatus* st, int64_t m_cap) {
   const unsigned long long m = st->m_needed;
   return m < (unsigned long long)m_cap ? (int64_t)m : m_cap;
 }
 
-__global__ void __launch_bounds__(RADIX_THREADS) k_radix_hist(const unsigned int* keys,
-                                                              const DevStatus* st, int64_t m_cap,
-                                                              int shift, unsigned int* hist,
-                                                              int64_t nblocks) {
-  __shared__ unsigned int cnt[RADIX_DIGITS];
-  for (int d = threadIdx.x; d < RADIX_DIGITS; d += blockDim.x) cnt[d] = 0;
-  __syncthreads();
+// [a, b) of tile t in the list, clipped to the stored intersections.
+__device__ __forceinline__ void tile_segment(const unsigned long long* toff, int t, int T,
+                                             const DevStatus* st, int64_t m_cap, int64_t& a,
+                                             int64_t& b) {
   const int64_t M = live_items(st, m_cap);
-  const int64_t base = (int64_t)blockIdx.x * RADIX_ITEMS;
-  if (base < M) {
-#pragma unroll 4
-    for (int k = 0; k < RADIX_PER_THREAD; ++k) {
-      const int64_t i = base + (int64_t)k * RADIX_THREADS + threadIdx.x;
-      if (i < M) atomicAdd(&cnt[(keys[i] >> shift) & (RADIX_DIGITS - 1)], 1u);
-    }
-  }
-  __syncthreads();
-  for (int d = threadIdx.x; d < RADIX_DIGITS; d += blockDim.x)
-    hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
+  a = (int64_t)toff[t];
+  b = t + 1 < T ? (int64_t)toff[t + 1] : (int64_t)st->m_needed;
+  a = a < M ? a : M;
+  b = b < M ? b : M;
 }
 
-__global__ void __launch_bounds__(RADIX_THREADS) k_radix_scatter(
-    const unsigned int* keys_in, const unsigned int* vals_in, unsigned int* keys_out,
-    unsigned int* vals_out, const DevStatus* st, int64_t m_cap, int shift,
-    const unsigned int* hist, int64_t nblocks) {
-  constexpr int WARPS = RADIX_THREADS / 32;
-  constexpr int PER_WARP = RADIX_ITEMS / WARPS;  // contiguous items per warp
-  constexpr int ROUNDS = PER_WARP / 32;
-  __shared__ unsigned int wcnt[WARPS][RADIX_DIGITS];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t M = live_items(st, m_cap);
-  const int64_t base = (int64_t)blockIdx.x * RADIX_ITEMS;
-  if (base >= M) return;  // whole block idle (uniform)
-  for (int d = lane; d < RADIX_DIGITS; d += 32) wcnt[warp][d] = 0;
+constexpr int SEG_WARP_MAX = 1024;  // longest segment one warp sorts in shared memory
+constexpr int SEG_BIG_CHUNK = 4096; // run length a CTA sorts in shared memory
+
+// One warp per tile: ascending sort of the tile's Gaussian indices.
+__global__ void __launch_bounds__(256) k_segsort(unsigned int* vals,
+                                                 const unsigned long long* toff, int T,
+                                                 DevStatus* st, int64_t m_cap, int* big) {
+  __shared__ unsigned int sh[8][SEG_WARP_MAX];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * 8 + warp;
+  if (t >= T) return;
+  int64_t a, b;
+  tile_segment(toff, t, T, st, m_cap, a, b);
+  const int L = (int)(b - a);
+  if (L <= 1) return;
+  if (L > SEG_WARP_MAX) {
+    if (lane == 0) big[atomicAdd(&st->big_cnt, 1u)] = t;
+    return;
+  }
+  if (L <= 32) {  // bitonic network across the lanes
+    unsigned int v = lane < L ? vals[a + lane] : 0xffffffffu;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const unsigned int u = __shfl_xor_sync(FULL_MASK, v, j);
+        const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+        v = keep_min ? min(v, u) : max(v, u);
+      }
+    }
+    if (lane < L) vals[a + lane] = v;
+    return;
+  }
+  int P = 64;
+  while (P < L) P <<= 1;
+  unsigned int* w = sh[warp];
+  for (int i = lane; i < P; i += 32) w[i] = i < L ? vals[a + i] : 0xffffffffu;
   __syncwarp();
-  const unsigned lt_mask = (1u << lane) - 1u;
-  unsigned int key[ROUNDS], val[ROUNDS];
-  const int64_t wbase = base + (int64_t)warp * PER_WARP;
-#pragma unroll
-  for (int r = 0; r < ROUNDS; ++r) {
-    const int64_t i = wbase + r * 32 + lane;
-    const bool valid = i < M;
-    key[r] = valid ? keys_in[i] : 0u;
-    val[r] = valid ? vals_in[i] : 0u;
-    const unsigned d = valid ? ((key[r] >> shift) & (RADIX_DIGITS - 1)) : RADIX_DIGITS;
-    const unsigned peers = __match_any_sync(FULL_MASK, d);
-    if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
-    __syncwarp();
-  }
-  __syncthreads();
-  for (int d = threadIdx.x; d < RADIX_DIGITS; d += blockDim.x) {
-    unsigned int run = hist[(int64_t)d * nblocks + blockIdx.x];
-#pragma unroll
-    for (int w = 0; w < WARPS; ++w) {
-      const unsigned int t = wcnt[w][d];
-      wcnt[w][d] = run;
-      run += t;
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < P; i += 32) {
+        const int l = i ^ j;
+        if (l > i) {
+          const unsigned int x = w[i], y = w[l];
+          if ((x > y) == ((i & k) == 0)) {
+            w[i] = y;
+            w[l] = x;
+          }
+        }
+      }
+      __syncwarp();
     }
   }
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < ROUNDS; ++r) {
-    const int64_t i = wbase + r * 32 + lane;
-    const bool valid = i < M;
-    const unsigned d = valid ? ((key[r] >> shift) & (RADIX_DIGITS - 1)) : RADIX_DIGITS;
-    const unsigned peers = __match_any_sync(FULL_MASK, d);
-    unsigned int pos = 0;
-    if (valid) pos = wcnt[warp][d] + __popc(peers & lt_mask);
-    __syncwarp();
-    if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] += __popc(peers);
-    __syncwarp();
-    if (valid && pos < (unsigned int)M) {
-      keys_out[pos] = key[r];
-      vals_out[pos] = val[r];
+  for (int i = lane; i < L; i += 32) vals[a + i] = w[i];
+}
+
+// Long segments, one CTA each: runs of SEG_BIG_CHUNK sorted in shared memory,
+// then pairwise merges between vals and tmp, each element placed by its rank
+// (its index in its own run plus a binary search in the other run; indices
+// are distinct, so the ranks are a permutation).
+__global__ void __launch_bounds__(1024) k_segsort_big(unsigned int* vals, unsigned int* tmp,
+                                                      const unsigned long long* toff, int T,
+                                                      const DevStatus* st, int64_t m_cap,
+                                                      const int* big) {
+  __shared__ unsigned int sh[SEG_BIG_CHUNK];
+  const unsigned int nbig = st->big_cnt;
+  for (unsigned int bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+    const int t = big[bi];
+    int64_t a, b;
+    tile_segment(toff, t, T, st, m_cap, a, b);
+    const int L = (int)(b - a);
+    for (int c0 = 0; c0 < L; c0 += SEG_BIG_CHUNK) {
+      const int n = min(SEG_BIG_CHUNK, L - c0);
+      __syncthreads();
+      for (int i = threadIdx.x; i < SEG_BIG_CHUNK; i += blockDim.x)
+        sh[i] = i < n ? vals[a + c0 + i] : 0xffffffffu;
+      __syncthreads();
+      for (int k = 2; k <= SEG_BIG_CHUNK; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+          for (int i = threadIdx.x; i < SEG_BIG_CHUNK; i += blockDim.x) {
+            const int l = i ^ j;
+            if (l > i) {
+              const unsigned int x = sh[i], y = sh[l];
+              if ((x > y) == ((i & k) == 0)) {
+                sh[i] = y;
+                sh[l] = x;
+              }
+            }
+          }
+          __syncthreads();
+        }
+      }
+      for (int i = threadIdx.x; i < n; i += blockDim.x) vals[a + c0 + i] = sh[i];
     }
+    __syncthreads();
+    unsigned int* src = vals + a;
+    unsigned int* dst = tmp + a;
+    for (int run = SEG_BIG_CHUNK; run < L; run <<= 1) {
+      for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const int r0 = (i / (2 * run)) * (2 * run);
+        const bool first = i - r0 < run;
+        const int o0 = first ? r0 + run : r0;          // the other run
+        const int o1 = first ? min(r0 + 2 * run, L) : r0 + run;
+        const unsigned int v = src[i];
+        int lo = o0, hi = o1;                          // elements of the other run below v
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (src[mid] < v) lo = mid + 1; else hi = mid;
+        }
+        const int own = first ? i - r0 : i - (r0 + run);
+        dst[r0 + own + (lo - o0)] = v;
+      }
+      __syncthreads();
+      unsigned int* x = src;
+      src = dst;
+      dst = x;
+    }
+    if (src != vals + a)
+      for (int i = threadIdx.x; i < L; i += blockDim.x) vals[a + i] = src[i];
+    __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------- ranges
 
-__global__ void __launch_bounds__(256) k_ranges(const unsigned int* keys, int2* range, int T,
-                                                const DevStatus* st, int64_t m_cap) {
-  const int64_t M = live_items(st, m_cap);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned int k = keys[i];
-    if (k >= (unsigned int)T) continue;
-    if (i == 0 || keys[i - 1] != k) range[k].x = (int)i;
-    if (i == M - 1 || keys[i + 1] != k) range[k].y = (int)(i + 1);
+__global__ void __launch_bounds__(256) k_ranges(const unsigned long long* toff, int2* range,
+                                                int T, const DevStatus* st, int64_t m_cap) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+    int64_t a, b;
+    tile_segment(toff, t, T, st, m_cap, a, b);
+    range[t] = make_int2((int)a, (int)b);
   }
 }
 
@@ -431,36 +483,37 @@ cudaError_t launch_scan_u32_to_u64(const unsigned int* in, unsigned long long* o
   return scan_exclusive<unsigned int, unsigned long long>(in, out, n, part, total, s);
 }
 
-cudaError_t launch_radix_sort(unsigned int* keys0, unsigned int* vals0, unsigned int* keys1,
-                              unsigned int* vals1, unsigned int* hist,
-                              unsigned long long* part, int64_t hist_blocks, int passes,
-                              int64_t m_cap, DevStatus* status, cudaStream_t s,
-                              unsigned int** keys_out, unsigned int** vals_out) {
-  unsigned int* kb[2] = {keys0, keys1};
-  unsigned int* vb[2] = {vals0, vals1};
-  for (int pass = 0; pass < passes; ++pass) {
-    const int shift = pass * RADIX_BITS;
-    const int src = pass & 1, dst = src ^ 1;
-    k_radix_hist<<<(unsigned)hist_blocks, RADIX_THREADS, 0, s>>>(kb[src], status, m_cap, shift,
-                                                                  hist, hist_blocks);
-    cudaError_t e = scan_exclusive<unsigned int, unsigned int>(
-        hist, hist, hist_blocks * RADIX_DIGITS, part, nullptr, s);
-    if (e != cudaSuccess) return e;
-    k_radix_scatter<<<(unsigned)hist_blocks, RADIX_THREADS, 0, s>>>(
-        kb[src], vb[src], kb[dst], vb[dst], status, m_cap, shift, hist, hist_blocks);
-  }
-  *keys_out = kb[passes & 1];
-  *vals_out = vb[passes & 1];
+cudaError_t run_binning(const PrepParams& p, int dtype, int T, unsigned long long* part,
+                        int2* range, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(p.tcnt, 0, sizeof(unsigned int) * (size_t)T, s);
+  if (e != cudaSuccess) return e;
+  if ((e = launch_preprocess(p, dtype, s)) != cudaSuccess) return e;
+  if ((e = launch_scan_u32_to_u64(p.tcnt, p.toff, T, part, &p.status->m_needed, s)) !=
+      cudaSuccess)
+    return e;
+  if ((e = launch_emit(p, s)) != cudaSuccess) return e;
+  if ((e = launch_segsort(p.vals, p.tmp, p.toff, T, p.status, p.m_cap, p.big, s)) !=
+      cudaSuccess)
+    return e;
+  return launch_ranges(p.toff, range, T, p.m_cap, p.H, p.W, p.tile,
+                       p.img_of ? 0 : p.tiles_x, p.status, s);
+}
+
+cudaError_t launch_segsort(unsigned int* vals, unsigned int* tmp,
+                           const unsigned long long* toff, int T, DevStatus* status,
+                           int64_t m_cap, int* big, cudaStream_t s) {
+  if (T == 0) return cudaSuccess;
+  k_segsort<<<(unsigned)((T + 7) / 8), 256, 0, s>>>(vals, toff, T, status, m_cap, big);
+  k_segsort_big<<<148, 1024, 0, s>>>(vals, tmp, toff, T, status, m_cap, big);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ranges(const unsigned int* keys, int2* range, int T, int64_t m_cap, int H,
-                          int W, int tile, int tiles_x, DevStatus* status, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(range, 0, sizeof(int2) * (size_t)T, s);
-  if (e != cudaSuccess) return e;
-  int64_t want = (m_cap + 255) / 256;
-  const unsigned grid = (unsigned)(want < 148 * 8 ? (want > 0 ? want : 1) : 148 * 8);
-  k_ranges<<<grid, 256, 0, s>>>(keys, range, T, status, m_cap);
+cudaError_t launch_ranges(const unsigned long long* toff, int2* range, int T, int64_t m_cap,
+                          int H, int W, int tile, int tiles_x, DevStatus* status,
+                          cudaStream_t s) {
+  if (T == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::min<int64_t>((T + 255) / 256, 148 * 8);
+  k_ranges<<<grid, 256, 0, s>>>(toff, range, T, status, m_cap);
   if (tiles_x > 0) {  // single image; the batched form counts its evaluations itself
     const unsigned g2 = (unsigned)std::min<int64_t>((T + 255) / 256, 148 * 4);
     k_tile_evals<<<g2 > 0 ? g2 : 1, 256, 0, s>>>(range, T, H, W, tile, tiles_x, status);

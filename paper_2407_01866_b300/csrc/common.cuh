@@ -31,7 +31,8 @@ struct DevStatus {
   unsigned long long m_needed;  // total intersections M
   unsigned long long evals;     // sum_j |S_j| * pixels(j)
   double loss_sum;              // sum |c_r - c_t| of the fused backward
-  unsigned int pad[8];
+  unsigned int big_cnt;         // tiles whose list is sorted by whole CTAs
+  unsigned int pad[7];
 };
 static_assert(sizeof(DevStatus) == 64, "status block is 64 bytes");
 

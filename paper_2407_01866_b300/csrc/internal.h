@@ -9,12 +9,6 @@
 
 namespace igs {
 
-// Radix sort geometry: one block scatters RADIX_THREADS * RADIX_PER_THREAD keys.
-constexpr int RADIX_THREADS = 256;
-constexpr int RADIX_PER_THREAD = 16;
-constexpr int RADIX_ITEMS = RADIX_THREADS * RADIX_PER_THREAD;
-constexpr int RADIX_BITS = 8;
-constexpr int RADIX_DIGITS = 1 << RADIX_BITS;
 // Scan geometry: one block scans SCAN_THREADS * SCAN_PER_THREAD entries.
 constexpr int SCAN_THREADS = 512;
 constexpr int SCAN_PER_THREAD = 8;
@@ -22,11 +16,10 @@ constexpr int SCAN_ITEMS = SCAN_THREADS * SCAN_PER_THREAD;
 
 // Byte offsets of the workspace sections (all 256-byte aligned).
 struct WsLayout {
-  size_t status, rec, trig, color, cnt, off, part, keys0, keys1, vals0, vals1, hist, range;
+  size_t status, rec, trig, color, tcnt, toff, part, vals, tmp, big, range;
   size_t total;
-  int64_t hist_blocks;  // radix blocks at full capacity
   int64_t part_len;     // scan partials entries
-  int tiles_x, tiles_y, passes;
+  int tiles_x, tiles_y;
 };
 WsLayout ws_layout(int64_t N, int n, int H, int W, int tile, int64_t m_cap);
 // Same layout for T tiles in total (batched form: tiles of all images).
@@ -45,10 +38,11 @@ struct PrepParams {
   GRec* rec;
   float2* trig;
   float* color_out;
-  unsigned int* cnt;
-  unsigned long long* off;
-  unsigned int* keys;
-  unsigned int* vals;
+  unsigned int* tcnt;           // [T] hits per tile (zeroed before preprocess)
+  unsigned long long* toff;     // [T] start of each tile's segment
+  unsigned int* vals;           // [m_cap] Gaussian index per intersection
+  unsigned int* tmp;            // [m_cap] merge buffer of long segments
+  int* big;                     // [T] tiles whose segment is sorted by a CTA
   int64_t m_cap;
   DevStatus* status;
   // batched form: image of each Gaussian, per-image (H, W, tiles_x, tiles_y)
@@ -103,14 +97,16 @@ cudaError_t launch_tile_evals_batch(const int2* range, int T, const int4* dims,
 cudaError_t launch_scan_u32_to_u64(const unsigned int* in, unsigned long long* out, int64_t n,
                                    unsigned long long* part, unsigned long long* total,
                                    cudaStream_t s);
-cudaError_t launch_radix_sort(unsigned int* keys0, unsigned int* vals0, unsigned int* keys1,
-                              unsigned int* vals1, unsigned int* hist,
-                              unsigned long long* part, int64_t hist_blocks, int passes,
-                              int64_t m_cap, DevStatus* status, cudaStream_t s,
-                              unsigned int** keys_out, unsigned int** vals_out);
-cudaError_t launch_ranges(const unsigned int* keys, int2* range, int T, int64_t m_cap,
+cudaError_t launch_segsort(unsigned int* vals, unsigned int* tmp,
+                           const unsigned long long* toff, int T, DevStatus* status,
+                           int64_t m_cap, int* big, cudaStream_t s);
+cudaError_t launch_ranges(const unsigned long long* toff, int2* range, int T, int64_t m_cap,
                           int H, int W, int tile, int tiles_x, DevStatus* status,
                           cudaStream_t s);
+// Whole binning sequence after the status reset: per-tile counts, scan,
+// emit, segment sort, ranges (and, for one image, the evaluation count).
+cudaError_t run_binning(const PrepParams& p, int dtype, int T, unsigned long long* part,
+                        int2* range, cudaStream_t s);
 
 // Render family: return cudaErrorInvalidValue for an unsupported (tile, K, n).
 cudaError_t launch_render_fwd(const RenderParams& p, int tile, int K, cudaStream_t s);

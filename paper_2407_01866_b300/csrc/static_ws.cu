@@ -76,8 +76,8 @@ extern "C" int igs_render_forward_static(const igs_gaussians* g, int32_t H, int3
     set_last_error(msg);
     return IGS_ERR_CAPACITY;
   }
-  // Each intersection costs 16 bytes of keys/values plus 1/16 byte of histogram.
-  int64_t m_cap = (int64_t)((STATIC_SCRATCH_BYTES - fixed) / 17);
+  // Each intersection costs 8 bytes: its list entry and a merge slot.
+  int64_t m_cap = (int64_t)((STATIC_SCRATCH_BYTES - fixed) / 8);
   size_t need = 0;
   while (m_cap > 1) {
     if (int r = igs_workspace_size(g->N, g->n, H, W, cfg, m_cap, &need)) return r;

@@ -40,6 +40,7 @@ CASES = [
     (33, 17, 60, 3, 1, 16, 6, (0.5, 8.0)),
     (16, 16, 1, 3, 10, 16, 7, (0.5, 8.0)),          # single Gaussian
     (1, 1, 5, 3, 2, 8, 8, (0.5, 8.0)),              # one pixel
+    (32, 32, 9000, 1, 4, 16, 9, (12.0, 40.0)),      # lists > 4096: CTA sort with merges
 ]
 
 
