@@ -184,95 +184,34 @@ __device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, fl
 // winning (candidate, pixel) pairs, split evenly over the CTA's threads.
 // ---------------------------------------------------------------------------
 
-// Near-first orders. A candidate is "near" for a warp when its key at the
-// centre of the warp's 8 x 4 block is below a bound; near candidates come
-// first (list order), the others after them (reverse list order). The order
-// only changes how soon thresholds tighten and when pass B may stop; the
-// selected sets do not depend on it.
-constexpr float NEAR_A = 36.0f;   // pass A: meet likely winners first
-constexpr float NEAR_B = 100.0f;  // pass B: all winners of a warp are near, usually
-
-template <int TILE>
-__device__ __forceinline__ float2 block_centre(int x0, int y0) {
-  constexpr int BPR = TILE / 8;
-  const int w = threadIdx.x >> 5;
-  return make_float2((float)(x0 + (w % BPR) * 8 + 4), (float)(y0 + (w / BPR) * 4 + 2));
-}
-
-// Fills this warp's ordA / ordB; returns how many candidates are near for B.
-__device__ __forceinline__ int near_orders(int cnt, float cx, float cy, const float4* s_a,
-                                           const float* s_a11, short* ordA, short* ordB) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  int nA = 0, fA = 0, nB = 0, fB = 0;
-  for (int base = 0; base < cnt; base += 32) {
-    const int j = base + lane;
-    const bool valid = j < cnt;
-    float key = F_INF;
-    if (valid) {
-      const float4 a = s_a[j];
-      key = rank_key(cx, cy, a.x, a.y, a.z, a.w, s_a11[j]);
-    }
-    const bool na = valid && key < NEAR_A, nb = valid && key < NEAR_B;
-    const unsigned bv = __ballot_sync(FULL_MASK, valid);
-    const unsigned ba = __ballot_sync(FULL_MASK, na);
-    const unsigned bb = __ballot_sync(FULL_MASK, nb);
-    if (valid) {
-      if (na) ordA[nA + __popc(ba & lt)] = (short)j;
-      else ordA[cnt - 1 - (fA + __popc(bv & ~ba & lt))] = (short)j;
-      if (nb) ordB[nB + __popc(bb & lt)] = (short)j;
-      else ordB[cnt - 1 - (fB + __popc(bv & ~bb & lt))] = (short)j;
-    }
-    nA += __popc(ba);
-    fA += __popc(bv & ~ba);
-    nB += __popc(bb);
-    fB += __popc(bv & ~bb);
-  }
-  __syncwarp();
-  return nB;
-}
-
-// Pass A over the staged list in the order `ord` (keys only). `tie` is set
-// when a candidate whose key equals the final threshold tau was dropped (a
-// boundary tie); without one, the winners are exactly the keys <= tau.
+// Pass A over the staged list (list order, keys only).
 template <int K>
 __device__ __forceinline__ void staged_keys(int cnt, float px, float py, const float4* s_a,
-                                            const float* s_a11, const short* ord,
-                                            float (&tq)[K], bool& tie) {
+                                            const float* s_a11, float (&tq)[K]) {
 #pragma unroll
   for (int k = 0; k < K; ++k) tq[k] = F_INF;
-  float v_drop = F_INF;
-#pragma unroll 2
-  for (int o = 0; o < cnt; ++o) {
-    const int j = ord[o];
+#pragma unroll 4
+  for (int j = 0; j < cnt; ++j) {
     const float4 a = s_a[j];
     const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_a11[j]);
-    const float thr = tq[K - 1];
-    const bool better = q < thr;
-    if (q == thr) v_drop = fminf(v_drop, q);  // rejected at the threshold
+    const bool better = q < tq[K - 1];
     if (__any_sync(FULL_MASK, better)) {
-      float x = better ? q : F_INF;  // +inf (and NaN) insert nothing
+      float x = better ? q : F_INF;
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const float lo = fminf(tq[k], x);
         x = fmaxf(tq[k], x);
         tq[k] = lo;
       }
-      if (better && tq[K - 1] == thr) v_drop = fminf(v_drop, thr);  // evicted at it
     }
   }
-  tie = tq[K - 1] < F_INF && v_drop == tq[K - 1];
 }
 
-// Pass B over the staged list. Without a boundary tie in the warp the
-// winners are the keys <= tau: the near group of `ordB` is visited first and
-// the rest only if some lane still misses a winner. A warp with a tie walks
-// the list in order with the exact (q, index) rule. With MASK, the ballot of
-// winning live pixels per candidate goes to mask_w[] (zeroed beforehand).
-template <int K, int NC, int CH, bool MASK>
+// Pass B over the staged list: exact (q, index) membership, blend, and the
+// ballot of winning live pixels of this warp per candidate into mask_w[].
+template <int K, int NC, int CH>
 __device__ __forceinline__ void staged_blend(const RenderParams& p, int cnt, float px, float py,
-                                             bool live, const float (&tq)[K], bool warp_tie,
-                                             const short* ordB, int nearB, const float4* s_a,
+                                             bool live, const float (&tq)[K], const float4* s_a,
                                              const float* s_a11, const int* s_gid,
                                              const float* s_col, unsigned* mask_w,
                                              PixelBlend<Chan<NC>::R>& r) {
@@ -281,56 +220,33 @@ __device__ __forceinline__ void staged_blend(const RenderParams& p, int cnt, flo
   const int lane = threadIdx.x & 31;
   r.q0 = tq[0];
   r.tau = tq[K - 1];
-  r.posK = 0x7fffffff;
+  r.posK = -1;
   r.Z = 0.0f;
 #pragma unroll
   for (int c = 0; c < NCR; ++c) r.cr[c] = 0.0f;
-  auto take = [&](int j, float q) {
-    const float w = blend_weight(r.q0, q);  // exactly 1 at q = q_min
-    r.Z += w;
+  int lt = 0;
 #pragma unroll
-    for (int c = 0; c < NCR; ++c)
-      if (NC > 0 || c < n)
-        r.cr[c] = fmaf(w, staged_colour<CH, NC>(p, s_col, s_gid, j, c), r.cr[c]);
-  };
-  if (!warp_tie) {
-    const int need = min(K, cnt);
-    int found = 0;
-    for (int o = 0; o < cnt; ++o) {
-      if (o == nearB && !__any_sync(FULL_MASK, found < need)) break;
-      const int j = ordB[o];
-      const float4 a = s_a[j];
-      const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_a11[j]);
-      const bool win = q <= r.tau;
-      if (MASK) {
-        const unsigned bal = __ballot_sync(FULL_MASK, win && live);
-        if (lane == 0) mask_w[j] = bal;
-      }
-      if (win) {
-        ++found;
-        take(j, q);
-      }
-    }
-  } else {
-    int lt = 0;
-#pragma unroll
-    for (int k = 0; k < K; ++k) lt += tq[k] < r.tau ? 1 : 0;
-    int eq_left = K - lt;
+  for (int k = 0; k < K; ++k) lt += tq[k] < r.tau ? 1 : 0;
+  int eq_left = K - lt;
 #pragma unroll 2
-    for (int j = 0; j < cnt; ++j) {
-      const float4 a = s_a[j];
-      const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_a11[j]);
-      bool win = q < r.tau;
-      if (q == r.tau && eq_left > 0) {
-        win = true;
-        --eq_left;
-        r.posK = j;
-      }
-      if (MASK) {
-        const unsigned bal = __ballot_sync(FULL_MASK, win && live);
-        if (lane == 0) mask_w[j] = bal;
-      }
-      if (win) take(j, q);
+  for (int j = 0; j < cnt; ++j) {
+    const float4 a = s_a[j];
+    const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_a11[j]);
+    bool win = q < r.tau;
+    if (q == r.tau && eq_left > 0) {
+      win = true;
+      --eq_left;
+      r.posK = j;
+    }
+    const unsigned bal = __ballot_sync(FULL_MASK, win && live);
+    if (lane == 0) mask_w[j] = bal;
+    if (win) {
+      const float w = blend_weight(r.q0, q);
+      r.Z += w;
+#pragma unroll
+      for (int c = 0; c < NCR; ++c)
+        if (NC > 0 || c < n)
+          r.cr[c] = fmaf(w, staged_colour<CH, NC>(p, s_col, s_gid, j, c), r.cr[c]);
     }
   }
   const float iz = r.Z > 0.0f ? 1.0f / r.Z : 0.0f;
@@ -345,30 +261,16 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(RenderParams p) {
   __shared__ float s_a11[NT];
   __shared__ int s_gid[NT];
   __shared__ float s_col[NT * (NC > 0 ? NC : 1)];
-  __shared__ short s_ord[NT / 32][2][NT];
   const int tile_id = blockIdx.x;
   const int tx = tile_id % p.tiles_x, ty = tile_id / p.tiles_x;
   const int2 lp = pixel_of<TILE>(threadIdx.x);
   const int x = tx * TILE + lp.x, y = ty * TILE + lp.y;
   const float px = (float)x + 0.5f, py = (float)y + 0.5f;
   const int2 range = p.range[tile_id];
-  const int len = range.y - range.x;
   float tq[K];
+  select_keys<TILE, K, NT>(p, range, px, py, tq, s_a, s_a11, s_gid);
   PixelBlend<Chan<NC>::R> r;
-  if (len <= NT) {  // the whole list fits one stage
-    stage_chunk<NT, NC>(p, range.x, len, s_a, s_a11, s_gid, s_col);
-    __syncthreads();
-    const int w = threadIdx.x >> 5;
-    const float2 c = block_centre<TILE>(tx * TILE, ty * TILE);
-    const int nearB = near_orders(len, c.x, c.y, s_a, s_a11, s_ord[w][0], s_ord[w][1]);
-    bool tie;
-    staged_keys<K>(len, px, py, s_a, s_a11, s_ord[w][0], tq, tie);
-    staged_blend<K, NC, NT, false>(p, len, px, py, true, tq, __any_sync(FULL_MASK, tie),
-                                   s_ord[w][1], nearB, s_a, s_a11, s_gid, s_col, nullptr, r);
-  } else {
-    select_keys<TILE, K, NT>(p, range, px, py, tq, s_a, s_a11, s_gid);
-    blend_pass<TILE, K, NC, NT>(p, range, px, py, tq, r, s_a, s_a11, s_gid, s_col);
-  }
+  blend_pass<TILE, K, NC, NT>(p, range, px, py, tq, r, s_a, s_a11, s_gid, s_col);
   if (x >= p.W || y >= p.H) return;
   const int n = nchan<NC>(p);
   const int64_t plane = (int64_t)p.H * p.W;
@@ -391,7 +293,7 @@ struct TileCtx {
 // Dynamic shared-memory layout of the adjoint kernel (in 4-byte words), for
 // NT pixels, n channels and CH Gaussians per stage.
 struct BwdSmem {
-  int a, a11, gid, col, ps0, ps1, gh, part, slotj, loss, scan, mask, ord, off, total;
+  int a, a11, gid, col, ps0, ps1, gh, part, slotj, loss, scan, mask, off, total;
 };
 __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   const int NWB = NT / 32;
@@ -409,7 +311,6 @@ __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   L.loss = o;  o += 2 * (NT / 32) + 2; // doubles
   L.scan = o;  o += 34;                // integer block-scan scratch
   L.mask = o;  o += NWB * CH;          // winner masks [warp block][candidate]
-  L.ord = o;   o += NWB * CH;          // shorts: two candidate orders per warp
   L.off = o;   o += NWB * CH + 1;      // pair offsets of (candidate, block) items
   L.total = o;
   return L;
@@ -653,7 +554,6 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   float* s_part = smem + SL.part;
   double* s_loss = reinterpret_cast<double*>(smem + SL.loss);
   unsigned* s_mask = reinterpret_cast<unsigned*>(smem + SL.mask);
-  short* s_ord = reinterpret_cast<short*>(smem + SL.ord);
   int* s_off = reinterpret_cast<int*>(smem + SL.off);
   int* s_slotj = reinterpret_cast<int*>(smem + SL.slotj);
 
@@ -670,18 +570,11 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   if (fast) {
     __syncthreads();  // the previous tile of a persistent CTA is done with smem
     stage_chunk<CH, NC>(p, range.x, len, s_a, s_a11, s_gid, s_col);
-    for (int i = threadIdx.x; i < NWB * CH; i += NT) s_mask[i] = 0u;
     __syncthreads();
     const int w = threadIdx.x >> 5;
-    short* ordA = s_ord + (2 * w) * CH;
-    short* ordB = ordA + CH;
-    const float2 c = block_centre<TILE>(t.x0, t.y0);
-    const int nearB = near_orders(len, c.x, c.y, s_a, s_a11, ordA, ordB);
-    bool tie;
-    staged_keys<K>(len, px, py, s_a, s_a11, ordA, tq, tie);
-    staged_blend<K, NC, CH, true>(p, len, px, py, x < t.W && y < t.H, tq,
-                                  __any_sync(FULL_MASK, tie), ordB, nearB, s_a, s_a11, s_gid,
-                                  s_col, s_mask + w * CH, r);
+    staged_keys<K>(len, px, py, s_a, s_a11, tq);
+    staged_blend<K, NC, CH>(p, len, px, py, x < t.W && y < t.H, tq, s_a, s_a11, s_gid, s_col,
+                            s_mask + w * CH, r);
   } else {
     select_keys<TILE, K, CH>(p, range, px, py, tq, s_a, s_a11, s_gid);
     blend_pass<TILE, K, NC, CH>(p, range, px, py, tq, r, s_a, s_a11, s_gid, s_col);
