@@ -311,7 +311,7 @@ __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   L.loss = o;  o += 2 * (NT / 32) + 2; // doubles
   L.scan = o;  o += 34;                // integer block-scan scratch
   L.mask = o;  o += NWB * CH;          // winner masks [warp block][candidate]
-  L.off = o;   o += NWB * CH + 1;      // pair offsets of (candidate, block) items
+  L.off = o;   o += (NWB * CH + 2) / 2;  // shorts: pair offsets of (candidate, block) items
   L.total = o;
   return L;
 }
@@ -388,7 +388,7 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
                                             const int* s_gid, const float* s_col,
                                             const unsigned* s_mask, const float4* s_ps0,
                                             const float2* s_ps1, const float* s_gh,
-                                            float* s_slot, int* s_slotj, int* s_off,
+                                            float* s_slot, int* s_slotj, short* s_off,
                                             int* s_scan) {
   constexpr int NT = TILE * TILE;
   constexpr int NWB = NT / 32;
@@ -407,10 +407,10 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
   int run = block_scan_int(loc, s_scan, P);
   for (int k = 0; k < per_it; ++k)
     if (i0 + k < nit) {
-      s_off[i0 + k] = run;
+      s_off[i0 + k] = (short)run;
       run += __popc(mask_of(i0 + k));
     }
-  if (threadIdx.x == 0) s_off[nit] = P;
+  if (threadIdx.x == 0) s_off[nit] = (short)P;  // P <= pixels * K <= 4096
   s_slotj[2 * threadIdx.x] = -1;
   s_slotj[2 * threadIdx.x + 1] = -1;
   __syncthreads();
@@ -554,7 +554,7 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   float* s_part = smem + SL.part;
   double* s_loss = reinterpret_cast<double*>(smem + SL.loss);
   unsigned* s_mask = reinterpret_cast<unsigned*>(smem + SL.mask);
-  int* s_off = reinterpret_cast<int*>(smem + SL.off);
+  short* s_off = reinterpret_cast<short*>(smem + SL.off);
   int* s_slotj = reinterpret_cast<int*>(smem + SL.slotj);
 
   const int2 lp = pixel_of<TILE>(threadIdx.x);
@@ -732,7 +732,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(RenderParams p) {
   t.off = 0;
   t.inv_count = p.inv_count;
   t.loss_acc = &p.status->loss_sum;
-  bwd_tile<TILE, K, NC, TILE * TILE>(p, t, smem);
+  bwd_tile<TILE, K, NC, TILE * TILE / 2>(p, t, smem);  // 128 Gaussians per stage at 16x16
 }
 
 __device__ __forceinline__ int image_of_tile(const BatchTables& bt, int tile) {
