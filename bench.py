@@ -95,6 +95,32 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
+def rank_env():
+    """(world size, rank, local rank) from the torchrun environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def rank_workload(w, rank):
+    """Each rank fits its own image: the same workload drawn with seed + rank."""
+    return dict(w, seed=w["seed"] + rank)
+
+
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """The slowest rank's mean step time; every rank must call it."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(ms, world):
+    """Whole-job steps per second: every rank completes one step per `ms`."""
+    return world * 1000.0 / ms
+
+
 def make_inputs(w=WORKLOAD):
     from paper_2407_01866_b300 import synth
     if w["n"] == 9:   # albedo RGB, normal XYZ in [-1, 1], roughness, metallic, AO
@@ -136,7 +162,7 @@ def cpu_baseline(target, P, budget_s=15.0, seed=0, w=WORKLOAD):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    rank = rank_env()[1]
     if rank != 0:
         return
     target, P = make_inputs()
@@ -164,9 +190,7 @@ def run_ours(args, w=WORKLOAD):
     import torch
     from paper_2407_01866_b300 import lib as L
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -174,7 +198,7 @@ def run_ours(args, w=WORKLOAD):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     H, W, n, N = w["H"], w["W"], w["n"], w["N"]
-    target_np, P_np = make_inputs(w)
+    target_np, P_np = make_inputs(rank_workload(w, rank))
     cfg = L.default_config()
     target = torch.from_numpy(target_np).to(dev)
     P0 = torch.from_numpy(P_np).to(dev)
@@ -234,10 +258,8 @@ def run_ours(args, w=WORKLOAD):
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     ms = float(statistics.mean(step_ms))
+    ms = max_over_ranks(ms, dist, dev)
     if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
 
     # binning statistics of the final state (evals of one forward)
@@ -282,7 +304,7 @@ def run_ours(args, w=WORKLOAD):
     e2e_ms = e0.elapsed_time(e1) / e_steps
 
     if rank == 0:
-        value = world * 1000.0 / ms
+        value = job_throughput(ms, world)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
