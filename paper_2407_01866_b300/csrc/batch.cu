@@ -135,6 +135,7 @@ int batch_bin(const igs_fit_state* st, const BatchGeom& G, const igs_config* cfg
   p.vals = reinterpret_cast<unsigned int*>(base + L.vals);
   p.tmp = reinterpret_cast<unsigned int*>(base + L.tmp);
   p.big = reinterpret_cast<int*>(base + L.big);
+  p.wide = reinterpret_cast<int*>(base + L.wide);
   p.m_cap = m_cap;
   p.status = status;
   p.img_of = reinterpret_cast<const int*>(base + G.img_of);

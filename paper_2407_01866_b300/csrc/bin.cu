@@ -34,6 +34,10 @@ __device__ __forceinline__ void tile_span(float m, float r, int tile, int tiles,
   hi = (int)b;
 }
 
+// A Gaussian whose tile box has more tiles than this is binned by a whole CTA
+// (threads stride over the box) instead of one thread.
+constexpr int WIDE_TILES = 32;
+
 // Image geometry of Gaussian i: the single image, or its image in a batch.
 struct ImgGeo {
   int H, W, tiles_x, tiles_y, tile_base;
@@ -80,6 +84,10 @@ __global__ void __launch_bounds__(256) k_preprocess(PrepParams p) {
     tile_span(mx, r, p.tile, ig.tiles_x, x0, x1);
     tile_span(my, r, p.tile, ig.tiles_y, y0, y1);
     const float r2 = __fmul_rn(r, r);
+    if ((x1 - x0 + 1) * (y1 - y0 + 1) > WIDE_TILES) {
+      p.wide[atomicAdd(&p.status->wide_cnt, 1u)] = (int)i;
+      y1 = y0 - 1;  // counted by k_count_wide
+    }
     for (int ty = y0; ty <= y1; ++ty) {
       const float Y0 = (float)(ty * p.tile), Y1 = (float)min((ty + 1) * p.tile, ig.H);
       for (int tx = x0; tx <= x1; ++tx) {
@@ -111,6 +119,7 @@ __global__ void __launch_bounds__(256) k_emit(PrepParams p) {
   int x0, x1, y0, y1;
   tile_span(mx, r, p.tile, ig.tiles_x, x0, x1);
   tile_span(my, r, p.tile, ig.tiles_y, y0, y1);
+  if ((x1 - x0 + 1) * (y1 - y0 + 1) > WIDE_TILES) return;  // emitted by k_emit_wide
   const float r2 = __fmul_rn(r, r);
   const unsigned long long cap = (unsigned long long)p.m_cap;
   for (int ty = y0; ty <= y1; ++ty) {
@@ -120,6 +129,40 @@ __global__ void __launch_bounds__(256) k_emit(PrepParams p) {
       if (circle_hits_rect(mx, my, r2, X0, X1, Y0, Y1)) {
         const int t = ig.tile_base + ty * ig.tiles_x + tx;
         // the counter runs back down from the tile's count: one slot per hit
+        const unsigned long long pos = p.toff[t] + (atomicSub(p.tcnt + t, 1u) - 1u);
+        if (pos < cap) p.vals[pos] = (unsigned int)i;
+      }
+    }
+  }
+}
+
+// Wide Gaussians, one CTA each: threads stride over the tile box and apply
+// the same circle-rectangle test. COUNT: increment the tile counters;
+// otherwise: take the tiles' slots (after the scan).
+template <bool BATCH, bool COUNT>
+__global__ void __launch_bounds__(256) k_wide(PrepParams p) {
+  const unsigned int nw = p.status->wide_cnt;
+  const unsigned long long cap = (unsigned long long)p.m_cap;
+  for (unsigned int wi = blockIdx.x; wi < nw; wi += gridDim.x) {
+    const int i = p.wide[wi];
+    const ImgGeo ig = image_geo<BATCH>(p, i);
+    const GRec g = p.rec[i];
+    const float mx = g.a.x, my = g.a.y, r = g.b.y;
+    int x0, x1, y0, y1;
+    tile_span(mx, r, p.tile, ig.tiles_x, x0, x1);
+    tile_span(my, r, p.tile, ig.tiles_y, y0, y1);
+    const float r2 = __fmul_rn(r, r);
+    const int bw = x1 - x0 + 1;
+    const int area = bw * (y1 - y0 + 1);
+    for (int k = threadIdx.x; k < area; k += blockDim.x) {
+      const int ty = y0 + k / bw, tx = x0 + k % bw;
+      const float Y0 = (float)(ty * p.tile), Y1 = (float)min((ty + 1) * p.tile, ig.H);
+      const float X0 = (float)(tx * p.tile), X1 = (float)min((tx + 1) * p.tile, ig.W);
+      if (!circle_hits_rect(mx, my, r2, X0, X1, Y0, Y1)) continue;
+      const int t = ig.tile_base + ty * ig.tiles_x + tx;
+      if (COUNT) {
+        atomicAdd(p.tcnt + t, 1u);
+      } else {
         const unsigned long long pos = p.toff[t] + (atomicSub(p.tcnt + t, 1u) - 1u);
         if (pos < cap) p.vals[pos] = (unsigned int)i;
       }
@@ -488,10 +531,15 @@ cudaError_t run_binning(const PrepParams& p, int dtype, int T, unsigned long lon
   cudaError_t e = cudaMemsetAsync(p.tcnt, 0, sizeof(unsigned int) * (size_t)T, s);
   if (e != cudaSuccess) return e;
   if ((e = launch_preprocess(p, dtype, s)) != cudaSuccess) return e;
+  const bool batch = p.img_of != nullptr;
+  if (batch) k_wide<true, true><<<148 * 4, 256, 0, s>>>(p);
+  else k_wide<false, true><<<148 * 4, 256, 0, s>>>(p);
   if ((e = launch_scan_u32_to_u64(p.tcnt, p.toff, T, part, &p.status->m_needed, s)) !=
       cudaSuccess)
     return e;
   if ((e = launch_emit(p, s)) != cudaSuccess) return e;
+  if (batch) k_wide<true, false><<<148 * 4, 256, 0, s>>>(p);
+  else k_wide<false, false><<<148 * 4, 256, 0, s>>>(p);
   if ((e = launch_segsort(p.vals, p.tmp, p.toff, T, p.status, p.m_cap, p.big, s)) !=
       cudaSuccess)
     return e;

@@ -32,7 +32,8 @@ struct DevStatus {
   unsigned long long evals;     // sum_j |S_j| * pixels(j)
   double loss_sum;              // sum |c_r - c_t| of the fused backward
   unsigned int big_cnt;         // tiles whose list is sorted by whole CTAs
-  unsigned int pad[7];
+  unsigned int wide_cnt;        // Gaussians whose tile box is binned by whole CTAs
+  unsigned int pad[6];
 };
 static_assert(sizeof(DevStatus) == 64, "status block is 64 bytes");
 

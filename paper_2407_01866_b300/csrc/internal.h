@@ -16,7 +16,7 @@ constexpr int SCAN_ITEMS = SCAN_THREADS * SCAN_PER_THREAD;
 
 // Byte offsets of the workspace sections (all 256-byte aligned).
 struct WsLayout {
-  size_t status, rec, trig, color, tcnt, toff, part, vals, tmp, big, range;
+  size_t status, rec, trig, color, tcnt, toff, part, vals, tmp, big, wide, range;
   size_t total;
   int64_t part_len;     // scan partials entries
   int tiles_x, tiles_y;
@@ -43,6 +43,7 @@ struct PrepParams {
   unsigned int* vals;           // [m_cap] Gaussian index per intersection
   unsigned int* tmp;            // [m_cap] merge buffer of long segments
   int* big;                     // [T] tiles whose segment is sorted by a CTA
+  int* wide;                    // [N] Gaussians whose tile box is binned by a CTA
   int64_t m_cap;
   DevStatus* status;
   // batched form: image of each Gaussian, per-image (H, W, tiles_x, tiles_y)
