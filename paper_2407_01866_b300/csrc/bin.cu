@@ -36,7 +36,7 @@ __device__ __forceinline__ void tile_span(float m, float r, int tile, int tiles,
 
 // A Gaussian whose tile box has more tiles than this is binned by a whole CTA
 // (threads stride over the box) instead of one thread.
-constexpr int WIDE_TILES = 32;
+constexpr int WIDE_TILES = 64;
 
 // Image geometry of Gaussian i: the single image, or its image in a batch.
 struct ImgGeo {
