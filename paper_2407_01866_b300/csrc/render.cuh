@@ -293,7 +293,7 @@ struct TileCtx {
 // Dynamic shared-memory layout of the adjoint kernel (in 4-byte words), for
 // NT pixels, n channels and CH Gaussians per stage.
 struct BwdSmem {
-  int a, a11, gid, col, ps0, ps1, gh, part, slotj, loss, scan, mask, off, total;
+  int a, a11, gid, col, ps0, ps1, gh, part, slotj, loss, scan, start, mask, off, total;
 };
 __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   const int NWB = NT / 32;
@@ -310,6 +310,7 @@ __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   L.slotj = o; o += 2 * NT;            // candidate held by each slot
   L.loss = o;  o += 2 * (NT / 32) + 2; // doubles
   L.scan = o;  o += 34;                // integer block-scan scratch
+  L.start = o; o += NT / 2;            // shorts: item where each thread's pair range starts
   L.mask = o;  o += NWB * CH;          // winner masks [warp block][candidate]
   L.off = o;   o += (NWB * CH + 2) / 2;  // shorts: pair offsets of (candidate, block) items
   L.total = o;
@@ -389,7 +390,7 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
                                             const unsigned* s_mask, const float4* s_ps0,
                                             const float2* s_ps1, const float* s_gh,
                                             float* s_slot, int* s_slotj, short* s_off,
-                                            int* s_scan) {
+                                            int* s_scan, short* s_start) {
   constexpr int NT = TILE * TILE;
   constexpr int NWB = NT / 32;
   constexpr int NCR = Chan<NC>::R;
@@ -405,31 +406,26 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
     if (i0 + k < nit) loc += __popc(mask_of(i0 + k));
   int P;
   int run = block_scan_int(loc, s_scan, P);
+  const int per = (P + NT - 1) / NT;  // pairs per thread
   for (int k = 0; k < per_it; ++k)
     if (i0 + k < nit) {
+      const int c = __popc(mask_of(i0 + k));
       s_off[i0 + k] = (short)run;
-      run += __popc(mask_of(i0 + k));
+      // the threads whose range starts inside this item begin here
+      for (int th = (run + per - 1) / max(per, 1); per > 0 && th * per < run + c; ++th)
+        s_start[th] = i0 + k;
+      run += c;
     }
   if (threadIdx.x == 0) s_off[nit] = (short)P;  // P <= pixels * K <= 4096
   s_slotj[2 * threadIdx.x] = -1;
   s_slotj[2 * threadIdx.x + 1] = -1;
   __syncthreads();
 
-  const int per = (P + NT - 1) / NT;
   const int r0 = (int)threadIdx.x * per;
   const int r1 = min(P, r0 + per);
   if (r0 < r1) {
-    auto item_of = [&](int e) {  // largest item whose offset is <= e
-      int lo = 0, hi = nit - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_off[mid] <= e) lo = mid; else hi = mid - 1;
-      }
-      return lo;
-    };
-    int it = item_of(r0);
+    int it = s_start[threadIdx.x];
     const int j_first = it / NWB;
-    const int j_last = item_of(r1 - 1) / NWB;
     unsigned m = mask_of(it);
     for (int k = r0 - s_off[it]; k > 0; --k) m &= m - 1;
     int j = j_first, wb = it - j * NWB;
@@ -446,8 +442,10 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
     float Tc[NCR];
 #pragma unroll
     for (int c = 0; c < NCR; ++c) Tc[c] = 0.0f;
-    auto flush = [&](int jj) {
-      if (jj == j_first || jj == j_last) {
+    // A candidate of a thread's range gets a slot if the range may not hold
+    // all of its pairs: the first one, and the one open when the range ends.
+    auto flush = [&](int jj, bool at_end) {
+      if (jj == j_first || at_end) {
         const int slot = 2 * (int)threadIdx.x + (jj == j_first ? 0 : 1);
         float* dst = s_slot + slot * np;
 #pragma unroll
@@ -498,7 +496,7 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
         const int nj = it / NWB;
         wb = it - nj * NWB;
         if (nj != j) {
-          flush(j);
+          flush(j, false);
           j = nj;
           a = s_a[j];
           a11 = s_a11[j];
@@ -506,7 +504,7 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
         }
       }
     }
-    flush(j);
+    flush(j, true);
   }
   __syncthreads();
   if ((int)threadIdx.x < cnt) {
@@ -621,7 +619,8 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   if (fast) {
     flat_pass_c<TILE, NC, CH>(p, t, len, s_a, s_a11, s_gid, s_col, s_mask, s_ps0, s_ps1, s_gh,
                               s_part,
-                              s_slotj, s_off, reinterpret_cast<int*>(smem + SL.scan));
+                              s_slotj, s_off, reinterpret_cast<int*>(smem + SL.scan),
+                              reinterpret_cast<short*>(smem + SL.start));
     return;
   }
   const int np = 5 + n;
