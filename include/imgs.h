@@ -91,9 +91,13 @@ typedef struct {
 } igs_gaussians;
 
 typedef struct {
-  int32_t K;          /* top-K, one of 1,2,3,4,8,10,16 (Sec. 4.1: 10) */
+  int32_t K;          /* top-K, one of 1,2,3,4,8,10,16 (Sec. 4.1: 10); 0 keeps
+                         all of S_j (the "no top-K" ablation of Table 1) */
   int32_t tile;       /* logical tile edge in px, 8 or 16 (Sec. 4.1: 16);
                          it changes S_j and therefore the image */
+  int32_t normalize;  /* 1: Eq. 5 (default). 0: the unnormalised sum
+                         c = sum G_i c_i over the kept Gaussians (Eq. 4
+                         restricted to S_j; Table 1 ablation) */
   /* fit step (Sec. 4.1): Adam learning rates per group */
   float lr_mu, lr_theta, lr_inv_scale, lr_color;
   double beta1, beta2;  /* double: 0.999 in float32 would move 1-beta2 by 1.3e-5 */

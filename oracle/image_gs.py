@@ -314,7 +314,7 @@ def selection(g, pts, H, W, K=10, tile=16):
 # Adjoint: gradients through the K retained Gaussians (Sec. 3.3).
 # ---------------------------------------------------------------------------
 
-def backward_points(g, pts, grad_out, H, W, K=10, tile=16):
+def backward_points(g, pts, grad_out, H, W, K=10, tile=16, normalize=True):
     """dL/dp for L with dL/dc_r(x) = grad_out[x] at the points pts, selection fixed.
 
     Returns float64 [N, 5+n] in the packed column order
@@ -324,6 +324,8 @@ def backward_points(g, pts, grad_out, H, W, K=10, tile=16):
       G_k = -(w_k / (2Z)) sum_ch g_ch (c_k,ch - c_r,ch)
       dq/dt1 = 2 t1 a^2, dq/dt2 = 2 t2 b^2, dq/dtheta = 2ab(t1^2 - t2^2)
       dq/dmu_px = -2 (t1^2 a u + t2^2 b v), dmu_px/dmu = (W, H).
+    Without normalisation (c_r = sum G_k c_k, G_k = exp(-q_k/2), the
+    ablation of Table 1): dL/dc_k = g G_k and G_k' = -(G_k/2) sum_ch g_ch c_k,ch.
     """
     pts = np.asarray(pts, dtype=F64).reshape(-1, 2)
     go = np.asarray(grad_out, dtype=F64).reshape(pts.shape[0], g.n)
@@ -340,14 +342,17 @@ def backward_points(g, pts, grad_out, H, W, K=10, tile=16):
     for (tx, ty), rows in groups.items():
         rows = np.asarray(rows)
         P = pts[rows]
-        cr, aux = _points_in_tile(g, P, tx, ty, tile, H, W, K, True, True)
+        cr, aux = _points_in_tile(g, P, tx, ty, tile, H, W, K, normalize, True)
         sel, w, Z = aux["sel"], aux["w"], aux["Z"]
         if sel.shape[1] == 0:
             continue
         gp = go[rows]                                          # [P, n]
         wz = w / Z[:, None]                                    # [P, K']
         ck = col[sel]                                          # [P, K', n]
-        Gq = -0.5 * wz * ((ck - cr[:, None, :]) * gp[:, None, :]).sum(axis=2)
+        if normalize:
+            Gq = -0.5 * wz * ((ck - cr[:, None, :]) * gp[:, None, :]).sum(axis=2)
+        else:
+            Gq = -0.5 * w * (ck * gp[:, None, :]).sum(axis=2)
         dx = P[:, 0:1] - mx32[sel].astype(F64)
         dy = P[:, 1:2] - my32[sel].astype(F64)
         c, s, a1, a2 = c64[sel], s64[sel], t1[sel], t2[sel]
@@ -370,17 +375,17 @@ def backward_points(g, pts, grad_out, H, W, K=10, tile=16):
     return grad
 
 
-def backward_pixels(g, pixels, grad_out, H, W, K=10, tile=16):
+def backward_pixels(g, pixels, grad_out, H, W, K=10, tile=16, normalize=True):
     """backward_points at integer pixels (h, w)."""
-    return backward_points(g, pixel_centres(pixels), grad_out, H, W, K, tile)
+    return backward_points(g, pixel_centres(pixels), grad_out, H, W, K, tile, normalize)
 
 
-def backward_image(g, grad_img, H, W, K=10, tile=16):
+def backward_image(g, grad_img, H, W, K=10, tile=16, normalize=True):
     """Adjoint of render_image for a planar upstream gradient [n, H, W]."""
     hh, ww = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
     pix = np.stack([hh.ravel(), ww.ravel()], axis=1)
     go = np.asarray(grad_img, dtype=F64).reshape(g.n, H * W).T
-    return backward_pixels(g, pix, go, H, W, K, tile)
+    return backward_pixels(g, pix, go, H, W, K, tile, normalize)
 
 
 # ---------------------------------------------------------------------------

@@ -46,6 +46,51 @@ __global__ void __launch_bounds__(256) k_adam(AdamParams a) {
   }
 }
 
+// Rows of a multiple of 4 floats: consecutive threads take consecutive float4
+// of the flattened arrays (coalesced), the columns follow from the index.
+template <int NP>
+__global__ void __launch_bounds__(256) k_adam_v4(AdamParams a) {
+  static_assert(NP % 4 == 0, "float4 rows");
+  __shared__ float s_bc[2];
+  if (threadIdx.x == 0) {
+    const int step = *a.step + 1;
+    s_bc[0] = (float)(1.0 - pow(a.b1d, (double)step));
+    s_bc[1] = (float)(1.0 - pow(a.b2d, (double)step));
+  }
+  __syncthreads();
+  const float inv_bc1 = 1.0f / s_bc[0];
+  const float inv_bc2 = 1.0f / s_bc[1];
+  const int64_t n4 = a.N * NP / 4;
+  float4* P4 = reinterpret_cast<float4*>(a.P);
+  const float4* G4 = reinterpret_cast<const float4*>(a.G);
+  float4* M4 = reinterpret_cast<float4*>(a.m);
+  float4* V4 = reinterpret_cast<float4*>(a.v);
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int col0 = (int)((q * 4) % NP);
+    float4 p = P4[q], g = G4[q], m = M4[q], v = V4[q];
+    float* pp = &p.x;
+    const float* gp = &g.x;
+    float* mp = &m.x;
+    float* vp = &v.x;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int col = col0 + k;
+      mp[k] = a.b1 * mp[k] + a.omb1 * gp[k];
+      vp[k] = a.b2 * vp[k] + a.omb2 * gp[k] * gp[k];
+      const float lr = col < 2 ? a.lr_mu : col == 2 ? a.lr_theta : col < 5 ? a.lr_t : a.lr_c;
+      float x = pp[k] - lr * (mp[k] * inv_bc1) / (sqrtf(vp[k] * inv_bc2) + a.eps);
+      if (col < 2) x = fminf(fmaxf(x, a.mu_min), a.mu_max);
+      else if (col == 2) x = fminf(fmaxf(x, a.theta_min), a.theta_max);
+      else if (col < 5) x = fminf(fmaxf(x, a.t_min), a.t_max);
+      pp[k] = x;
+    }
+    P4[q] = p;
+    M4[q] = m;
+    V4[q] = v;
+  }
+}
+
 __global__ void k_finalize(int32_t* step, DevStatus* st, float inv_count, float* loss_out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     *step += 1;
@@ -77,7 +122,18 @@ cudaError_t launch_adam(const AdamParams& a, cudaStream_t s) {
   if (blocks > 148 * 16) blocks = 148 * 16;
   switch (a.n) {
     case 1: k_adam<6><<<(unsigned)blocks, 256, 0, s>>>(a); break;
-    case 3: k_adam<8><<<(unsigned)blocks, 256, 0, s>>>(a); break;
+    case 3: {
+      const bool aligned16 = ((uintptr_t)a.P | (uintptr_t)a.G | (uintptr_t)a.m |
+                              (uintptr_t)a.v) % 16 == 0;
+      if (aligned16) {
+        int64_t b4 = (a.N * 2 + 255) / 256;
+        if (b4 > 148 * 16) b4 = 148 * 16;
+        k_adam_v4<8><<<(unsigned)b4, 256, 0, s>>>(a);
+      } else {
+        k_adam<8><<<(unsigned)blocks, 256, 0, s>>>(a);
+      }
+      break;
+    }
     case 4: k_adam<9><<<(unsigned)blocks, 256, 0, s>>>(a); break;
     case 9: k_adam<14><<<(unsigned)blocks, 256, 0, s>>>(a); break;
     default: k_adam<0><<<(unsigned)blocks, 256, 0, s>>>(a); break;

@@ -73,9 +73,11 @@ WsLayout ws_layout_tiles(int64_t N, int n, int64_t T, int64_t m_cap) {
 
 static int check_config(const igs_config* cfg, int n) {
   if (!cfg) return fail(IGS_ERR_INVALID_ARG, "config is NULL");
+  if (cfg->normalize != 0 && cfg->normalize != 1)
+    return fail(IGS_ERR_INVALID_ARG, "normalize must be 0 or 1");
   if (!render_supported(cfg->tile, cfg->K, n))
     return fail(IGS_ERR_INVALID_ARG,
-                "unsupported (tile=%d, K=%d, n=%d): tile 8 or 16, K in {1,2,3,4,8,10,16}, "
+                "unsupported (tile=%d, K=%d, n=%d): tile 8 or 16, K in {0,1,2,3,4,8,10,16}, "
                 "n in 1..32",
                 cfg->tile, cfg->K, n);
   return IGS_OK;
@@ -159,6 +161,7 @@ void igs_default_config(igs_config* c) {
   if (!c) return;
   c->K = 10;
   c->tile = 16;
+  c->normalize = 1;
   c->lr_mu = 5e-4f;
   c->lr_color = 5e-3f;
   c->lr_inv_scale = 2e-3f;
@@ -261,6 +264,7 @@ int igs_render_forward(const igs_bins* bins, const igs_config* cfg, float* d_img
   if (!d_img) return fail(IGS_ERR_INVALID_ARG, "image is NULL");
   if (!aligned(d_img, 4)) return fail(IGS_ERR_ALIGN, "image must be 4-byte aligned");
   RenderParams p = render_params(bins);
+  p.normalize = cfg->normalize;
   p.img = d_img;
   IGS_CUDA(launch_render_fwd(p, cfg->tile, cfg->K, reinterpret_cast<cudaStream_t>(stream)),
            "render_forward");
@@ -288,6 +292,7 @@ int igs_render_backward(const igs_gaussians* g, const igs_bins* bins, const igs_
   IGS_CUDA(cudaMemsetAsync(d_grad, 0, sizeof(float) * (size_t)g->N * (5 + g->n), s),
            "zero grad");
   RenderParams p = render_params(bins);
+  p.normalize = cfg->normalize;
   p.grad_img = d_grad_img;
   p.target = d_target;
   p.grad = d_grad;
@@ -371,6 +376,7 @@ int igs_decode_points(const igs_bins* bins, const igs_config* cfg, const float* 
   if (!aligned(d_xy, 4) || !aligned(d_out, 4))
     return fail(IGS_ERR_ALIGN, "float arrays must be 4-byte aligned");
   RenderParams p = render_params(bins);
+  p.normalize = cfg->normalize;
   p.qxy = d_xy;
   p.qout = d_out;
   p.Q = Q;

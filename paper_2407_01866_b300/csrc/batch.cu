@@ -186,6 +186,7 @@ int batch_adjoint(const igs_fit_state* st, const float* d_targets, const BatchGe
   BCUDA(cudaMemsetAsync(base + G.work, 0, sizeof(unsigned int), s), "batch: zero counter");
   rp.target = d_targets;
   rp.grad = st->grad;
+  rp.normalize = cfg->normalize;
   const BatchTables bt = tables(G, base, tn.order);
   BCUDA(launch_render_bwd_batch(rp, bt, cfg->K, tn.stage, tn.ctas_per_sm * sm_count(), s),
         "batch: adjoint");

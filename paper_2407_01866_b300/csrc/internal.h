@@ -61,6 +61,7 @@ struct RenderParams {
   const float* color;  // [N][n]
   int H, W, tiles_x, tiles_y, n;
   int N;                   // number of Gaussians (bounds guard on list entries)
+  int normalize;           // 1: Eq. 5; 0: unnormalised sum over the kept Gaussians
   float* img;              // forward output [n][H][W]
   const float* grad_img;   // backward upstream gradient or null
   const float* target;     // L1 target when grad_img is null

@@ -26,6 +26,9 @@
 
 namespace igs {
 
+// K = 0 selects all of S_j (no top-K): arrays keep one slot.
+template <int K> struct KS { static constexpr int A = K > 0 ? K : 1; };
+
 template <int NC> struct Chan { static constexpr int R = NC; };
 template <> struct Chan<0> { static constexpr int R = 32; };  // runtime n <= 32
 
@@ -88,10 +91,11 @@ __device__ __forceinline__ float staged_colour(const RenderParams& p, const floa
 // staged per round ("Gaussians per stage", CH <= TILE*TILE).
 template <int TILE, int K, int CH>
 __device__ __forceinline__ void select_keys(const RenderParams& p, int2 range, float px,
-                                            float py, float (&tq)[K], float4* s_a, float* s_a11,
-                                            int* s_gid) {
+                                            float py, float (&tq)[KS<K>::A], float4* s_a,
+                                            float* s_a11, int* s_gid) {
 #pragma unroll
-  for (int k = 0; k < K; ++k) tq[k] = F_INF;
+  for (int k = 0; k < KS<K>::A; ++k) tq[k] = F_INF;
+  if (K == 0 && !p.normalize) return;  // every candidate wins, no shift needed
   for (int base = range.x; base < range.y; base += CH) {
     const int cnt = min(CH, range.y - base);
     __syncthreads();
@@ -101,11 +105,15 @@ __device__ __forceinline__ void select_keys(const RenderParams& p, int2 range, f
     for (int j = 0; j < cnt; ++j) {
       const float4 a = s_a[j];
       const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_a11[j]);
-      const bool better = q < tq[K - 1];
+      if (K == 0) {  // all of S_j: only the smallest key is needed
+        tq[0] = fminf(tq[0], q);
+        continue;
+      }
+      const bool better = q < tq[KS<K>::A - 1];
       if (__any_sync(FULL_MASK, better)) {
         float x = better ? q : F_INF;  // +inf (and NaN) insert nothing
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
+        for (int k = 0; k < KS<K>::A; ++k) {
           const float lo = fminf(tq[k], x);
           x = fmaxf(tq[k], x);
           tq[k] = lo;
@@ -128,16 +136,16 @@ struct PixelBlend {
 // Pass B: exact top-K membership in list order and the blend of Eq. 5.
 template <int TILE, int K, int NC, int CH>
 __device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, float px,
-                                           float py, const float (&tq)[K],
+                                           float py, const float (&tq)[KS<K>::A],
                                            PixelBlend<Chan<NC>::R>& r, float4* s_a,
                                            float* s_a11, int* s_gid, float* s_col) {
   constexpr int NCR = Chan<NC>::R;
   const int n = nchan<NC>(p);
-  r.q0 = tq[0];
-  r.tau = tq[K - 1];
+  r.q0 = p.normalize ? tq[0] : 0.0f;  // unnormalised: w = exp(-q/2) itself
+  r.tau = K == 0 ? F_INF : tq[KS<K>::A - 1];
   int lt = 0;
 #pragma unroll
-  for (int k = 0; k < K; ++k) lt += tq[k] < r.tau ? 1 : 0;
+  for (int k = 0; k < KS<K>::A; ++k) lt += tq[k] < r.tau ? 1 : 0;
   int eq_left = K - lt;  // tau-valued slots still open
   r.posK = -1;
   r.Z = 0.0f;
@@ -171,7 +179,7 @@ __device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, fl
       }
     }
   }
-  const float iz = r.Z > 0.0f ? 1.0f / r.Z : 0.0f;
+  const float iz = p.normalize ? (r.Z > 0.0f ? 1.0f / r.Z : 0.0f) : 1.0f;
 #pragma unroll
   for (int c = 0; c < NCR; ++c) r.cr[c] *= iz;
 }
@@ -186,19 +194,25 @@ __device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, fl
 
 // Pass A over the staged list (list order, keys only).
 template <int K>
-__device__ __forceinline__ void staged_keys(int cnt, float px, float py, const float4* s_a,
-                                            const float* s_a11, float (&tq)[K]) {
+__device__ __forceinline__ void staged_keys(const RenderParams& p, int cnt, float px, float py,
+                                            const float4* s_a, const float* s_a11,
+                                            float (&tq)[KS<K>::A]) {
 #pragma unroll
-  for (int k = 0; k < K; ++k) tq[k] = F_INF;
+  for (int k = 0; k < KS<K>::A; ++k) tq[k] = F_INF;
+  if (K == 0 && !p.normalize) return;
 #pragma unroll 4
   for (int j = 0; j < cnt; ++j) {
     const float4 a = s_a[j];
     const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_a11[j]);
-    const bool better = q < tq[K - 1];
+    if (K == 0) {
+      tq[0] = fminf(tq[0], q);
+      continue;
+    }
+    const bool better = q < tq[KS<K>::A - 1];
     if (__any_sync(FULL_MASK, better)) {
       float x = better ? q : F_INF;
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
+      for (int k = 0; k < KS<K>::A; ++k) {
         const float lo = fminf(tq[k], x);
         x = fmaxf(tq[k], x);
         tq[k] = lo;
@@ -211,22 +225,22 @@ __device__ __forceinline__ void staged_keys(int cnt, float px, float py, const f
 // ballot of winning live pixels of this warp per candidate into mask_w[].
 template <int K, int NC, int CH>
 __device__ __forceinline__ void staged_blend(const RenderParams& p, int cnt, float px, float py,
-                                             bool live, const float (&tq)[K], const float4* s_a,
-                                             const float* s_a11, const int* s_gid,
-                                             const float* s_col, unsigned* mask_w,
-                                             PixelBlend<Chan<NC>::R>& r) {
+                                             bool live, const float (&tq)[KS<K>::A],
+                                             const float4* s_a, const float* s_a11,
+                                             const int* s_gid, const float* s_col,
+                                             unsigned* mask_w, PixelBlend<Chan<NC>::R>& r) {
   constexpr int NCR = Chan<NC>::R;
   const int n = nchan<NC>(p);
   const int lane = threadIdx.x & 31;
-  r.q0 = tq[0];
-  r.tau = tq[K - 1];
+  r.q0 = p.normalize ? tq[0] : 0.0f;
+  r.tau = K == 0 ? F_INF : tq[KS<K>::A - 1];
   r.posK = -1;
   r.Z = 0.0f;
 #pragma unroll
   for (int c = 0; c < NCR; ++c) r.cr[c] = 0.0f;
   int lt = 0;
 #pragma unroll
-  for (int k = 0; k < K; ++k) lt += tq[k] < r.tau ? 1 : 0;
+  for (int k = 0; k < KS<K>::A; ++k) lt += tq[k] < r.tau ? 1 : 0;
   int eq_left = K - lt;
 #pragma unroll 2
   for (int j = 0; j < cnt; ++j) {
@@ -249,7 +263,7 @@ __device__ __forceinline__ void staged_blend(const RenderParams& p, int cnt, flo
           r.cr[c] = fmaf(w, staged_colour<CH, NC>(p, s_col, s_gid, j, c), r.cr[c]);
     }
   }
-  const float iz = r.Z > 0.0f ? 1.0f / r.Z : 0.0f;
+  const float iz = p.normalize ? (r.Z > 0.0f ? 1.0f / r.Z : 0.0f) : 1.0f;
 #pragma unroll
   for (int c = 0; c < NCR; ++c) r.cr[c] *= iz;
 }
@@ -267,7 +281,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(RenderParams p) {
   const int x = tx * TILE + lp.x, y = ty * TILE + lp.y;
   const float px = (float)x + 0.5f, py = (float)y + 0.5f;
   const int2 range = p.range[tile_id];
-  float tq[K];
+  float tq[KS<K>::A];
   select_keys<TILE, K, NT>(p, range, px, py, tq, s_a, s_a11, s_gid);
   PixelBlend<Chan<NC>::R> r;
   blend_pass<TILE, K, NC, NT>(p, range, px, py, tq, r, s_a, s_a11, s_gid, s_col);
@@ -563,14 +577,14 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   // ---- passes A and B: per-pixel forward values and upstream gradient
   const int len = range.y - range.x;
   const bool fast = len <= CH;
-  float tq[K];
+  float tq[KS<K>::A];
   PixelBlend<NCR> r;
   if (fast) {
     __syncthreads();  // the previous tile of a persistent CTA is done with smem
     stage_chunk<CH, NC>(p, range.x, len, s_a, s_a11, s_gid, s_col);
     __syncthreads();
     const int w = threadIdx.x >> 5;
-    staged_keys<K>(len, px, py, s_a, s_a11, tq);
+    staged_keys<K>(p, len, px, py, s_a, s_a11, tq);
     staged_blend<K, NC, CH>(p, len, px, py, x < t.W && y < t.H, tq, s_a, s_a11, s_gid, s_col,
                             s_mask + w * CH, r);
   } else {
@@ -581,7 +595,7 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   float loss = 0.0f;
   const bool live = x < t.W && y < t.H && r.Z > 0.0f;
   float beta = 0.0f;
-  const float iz = live ? 1.0f / r.Z : 0.0f;
+  const float iz = live ? (p.normalize ? 1.0f / r.Z : 1.0f) : 0.0f;
   const int64_t plane = (int64_t)t.H * t.W;
   const int64_t o = t.off + (int64_t)y * t.W + x;
 #pragma unroll
@@ -598,7 +612,7 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
         }
       }
       const float gh = -0.5f * g * iz;  // dL/dq_k = w_k * (sum_c gh_c c_k,c - beta)
-      beta = fmaf(gh, r.cr[c], beta);
+      if (p.normalize) beta = fmaf(gh, r.cr[c], beta);
       s_gh[c * NT + threadIdx.x] = gh;
     }
   }
@@ -786,38 +800,63 @@ __global__ void __launch_bounds__(256) k_decode(RenderParams p) {
   const float fx = fminf(fmaxf(floorf(px * inv), 0.0f), (float)(p.tiles_x - 1));
   const float fy = fminf(fmaxf(floorf(py * inv), 0.0f), (float)(p.tiles_y - 1));
   const int2 range = p.range[(int)fy * p.tiles_x + (int)fx];
-  float tq[K];
-  int tp[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    tq[k] = F_INF;
-    tp[k] = -1;
-  }
-  for (int j = range.x; j < range.y; ++j) {
-    const int id = p.list[j];
-    if ((unsigned)id >= (unsigned)p.N) continue;
-    const GRec g = p.rec[id];
-    const float q = rank_key(px, py, g.a.x, g.a.y, g.a.z, g.a.w, g.b.x);
-    if (q < tq[K - 1]) topk_insert<K>(tq, tp, q, id);
-  }
   const int n = nchan<NC>(p);
   constexpr int NCR = Chan<NC>::R;
   float cr[NCR];
 #pragma unroll
   for (int c = 0; c < NCR; ++c) cr[c] = 0.0f;
   float Z = 0.0f;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (tp[k] >= 0) {
-      const float w = blend_weight(tq[0], tq[k]);
+  if (K == 0) {  // all of S_j
+    float q0 = 0.0f;
+    if (p.normalize) {
+      q0 = F_INF;
+      for (int j = range.x; j < range.y; ++j) {
+        const int id = p.list[j];
+        if ((unsigned)id >= (unsigned)p.N) continue;
+        const GRec g = p.rec[id];
+        q0 = fminf(q0, rank_key(px, py, g.a.x, g.a.y, g.a.z, g.a.w, g.b.x));
+      }
+    }
+    for (int j = range.x; j < range.y; ++j) {
+      const int id = p.list[j];
+      if ((unsigned)id >= (unsigned)p.N) continue;
+      const GRec g = p.rec[id];
+      const float w = blend_weight(q0, rank_key(px, py, g.a.x, g.a.y, g.a.z, g.a.w, g.b.x));
       Z += w;
-      const float* col = p.color + (int64_t)tp[k] * n;
+      const float* col = p.color + (int64_t)id * n;
 #pragma unroll
       for (int c = 0; c < NCR; ++c)
         if (NC > 0 || c < n) cr[c] = fmaf(w, col[c], cr[c]);
     }
+  } else {
+    float tq[KS<K>::A];
+    int tp[KS<K>::A];
+#pragma unroll
+    for (int k = 0; k < KS<K>::A; ++k) {
+      tq[k] = F_INF;
+      tp[k] = -1;
+    }
+    for (int j = range.x; j < range.y; ++j) {
+      const int id = p.list[j];
+      if ((unsigned)id >= (unsigned)p.N) continue;
+      const GRec g = p.rec[id];
+      const float q = rank_key(px, py, g.a.x, g.a.y, g.a.z, g.a.w, g.b.x);
+      if (q < tq[KS<K>::A - 1]) topk_insert<KS<K>::A>(tq, tp, q, id);
+    }
+    const float q0 = p.normalize ? tq[0] : 0.0f;
+#pragma unroll
+    for (int k = 0; k < KS<K>::A; ++k) {
+      if (tp[k] >= 0) {
+        const float w = blend_weight(q0, tq[k]);
+        Z += w;
+        const float* col = p.color + (int64_t)tp[k] * n;
+#pragma unroll
+        for (int c = 0; c < NCR; ++c)
+          if (NC > 0 || c < n) cr[c] = fmaf(w, col[c], cr[c]);
+      }
+    }
   }
-  const float iz = Z > 0.0f ? 1.0f / Z : 0.0f;
+  const float iz = p.normalize ? (Z > 0.0f ? 1.0f / Z : 0.0f) : 1.0f;
 #pragma unroll
   for (int c = 0; c < NCR; ++c)
     if (NC > 0 || c < n) p.qout[qi * n + c] = cr[c] * iz;
@@ -826,6 +865,7 @@ __global__ void __launch_bounds__(256) k_decode(RenderParams p) {
 // Dispatch over the supported K and channel counts.
 #define IGS_FOR_K(M, ...)                          \
   switch (K) {                                     \
+    case 0: M(0, __VA_ARGS__); break;              \
     case 1: M(1, __VA_ARGS__); break;              \
     case 2: M(2, __VA_ARGS__); break;              \
     case 3: M(3, __VA_ARGS__); break;              \
@@ -839,7 +879,7 @@ __global__ void __launch_bounds__(256) k_decode(RenderParams p) {
 #define IGS_NC_OF(n) ((n) == 1 ? 1 : (n) == 3 ? 3 : (n) == 4 ? 4 : (n) == 9 ? 9 : 0)
 
 inline bool k_supported(int K) {
-  return K == 1 || K == 2 || K == 3 || K == 4 || K == 8 || K == 10 || K == 16;
+  return K == 0 || K == 1 || K == 2 || K == 3 || K == 4 || K == 8 || K == 10 || K == 16;
 }
 
 }  // namespace igs

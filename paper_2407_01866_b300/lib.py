@@ -35,7 +35,7 @@ class Gaussians(ctypes.Structure):
 
 
 class Config(ctypes.Structure):
-    _fields_ = [("K", ctypes.c_int32), ("tile", ctypes.c_int32),
+    _fields_ = [("K", ctypes.c_int32), ("tile", ctypes.c_int32), ("normalize", ctypes.c_int32),
                 ("lr_mu", ctypes.c_float), ("lr_theta", ctypes.c_float),
                 ("lr_inv_scale", ctypes.c_float), ("lr_color", ctypes.c_float),
                 ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_float),

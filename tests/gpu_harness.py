@@ -14,9 +14,10 @@ def dev(a, dtype=torch.float32):
 class GpuSet:
     """Device copies of a parameter set plus its binning."""
 
-    def __init__(self, g, H, W, K=10, tile=16, dtype=torch.float32, m_capacity=None):
+    def __init__(self, g, H, W, K=10, tile=16, dtype=torch.float32, m_capacity=None,
+                 normalize=1):
         self.H, self.W, self.n, self.N = H, W, g.n, g.N
-        self.cfg = L.default_config(K=K, tile=tile)
+        self.cfg = L.default_config(K=K, tile=tile, normalize=normalize)
         self.xy = dev(g.xy, dtype)
         self.theta = dev(g.theta, dtype)
         self.inv_scale = dev(g.inv_scale, dtype)

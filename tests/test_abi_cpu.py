@@ -47,7 +47,7 @@ def test_every_declared_symbol_is_exported_and_bound(lib):
 def test_version_and_default_config(lib):
     assert L.version() == 10000
     c = L.default_config()
-    assert c.K == 10 and c.tile == 16
+    assert c.K == 10 and c.tile == 16 and c.normalize == 1
     assert abs(c.lr_mu - 5e-4) < 1e-9 and abs(c.lr_color - 5e-3) < 1e-9
     assert abs(c.lr_inv_scale - 2e-3) < 1e-9 and abs(c.lr_theta - 2e-3) < 1e-9
     assert abs(c.theta_max - 3.14159265) < 1e-6

@@ -182,3 +182,33 @@ def test_nonfinite_parameters_are_flagged_and_skipped():
     gk = O.Gaussians(g.xy[keep], g.theta[keep], g.inv_scale[keep], g.color[keep])
     want = O.render_image(gk, H, W)
     np.testing.assert_allclose(gs.forward(), want, atol=PIX_TOL)
+
+
+ABLATION = [
+    # (H, W, N, n, K, tile, normalize, seed)  K = 0: all of S_j
+    (64, 48, 300, 3, 0, 16, 1, 30),
+    (64, 48, 300, 3, 3, 16, 0, 31),
+    (40, 56, 200, 1, 0, 8, 0, 32),
+    (64, 64, 1200, 3, 0, 16, 1, 33),   # lists > 128 and > 256: staged chunks
+]
+
+
+@pytest.mark.parametrize("case", ABLATION, ids=lambda c: f"K{c[4]}_norm{c[6]}_t{c[5]}_N{c[2]}")
+def test_ablation_modes_forward_adjoint_decode(case):
+    """Table 1 ablations: all of S_j (K = 0) and/or no normalisation."""
+    H, W, N, n, K, tile, norm, seed = case
+    g = oset(N, n, seed, (1.0, 12.0) if N > 1000 else (0.5, 8.0))
+    Ko = None if K == 0 else K
+    gs = GpuSet(g, H, W, K, tile, normalize=norm)
+    want = O.render_image(g, H, W, K=Ko, tile=tile, normalize=bool(norm))
+    got = gs.forward()
+    scale = max(1.0, np.abs(want).max())
+    assert np.abs(got - want).max() <= PIX_TOL * scale
+    gimg = np.random.default_rng(seed).standard_normal((n, H, W)).astype(np.float32)
+    grad, _ = gs.backward(grad_img=gimg)
+    ref = O.backward_image(g, gimg, H, W, K=Ko, tile=tile, normalize=bool(norm))
+    errs = grad_rel_error(grad, ref)
+    assert max(errs.values()) <= GRAD_TOL, errs
+    pts = synth.query_points(500, H, W, seed=seed)
+    dec = O.render_points(g, pts.astype(np.float64), H, W, K=Ko, tile=tile, normalize=bool(norm))
+    assert np.abs(gs.decode(pts) - dec).max() <= PIX_TOL * scale

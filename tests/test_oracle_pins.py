@@ -298,12 +298,12 @@ def test_count_evals_equals_brute_force_pixel_sum():
 
 # ---------------------------------------------------------------- gradients
 
-def _fd_check(n, seed):
-    H, W, T, K = 24, 24, 8, 3
+def _fd_check(n, seed, K=3, normalize=True):
+    H, W, T = 24, 24, 8
     g = rand_set(12, n, seed, s_range=(1.5, 6.0))
     rng = np.random.default_rng(seed)
     gout = rng.standard_normal((n, H, W))
-    grad = O.backward_image(g, gout, H, W, K=K, tile=T)
+    grad = O.backward_image(g, gout, H, W, K=K, tile=T, normalize=normalize)
     P0 = g.packed().astype(np.float64)
     hh, ww = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
     pix = np.stack([hh.ravel(), ww.ravel()], 1)
@@ -318,7 +318,7 @@ def _fd_check(n, seed):
         sel = O.selection(gg, pts, H, W, K=K, tile=T)
         if any(not np.array_equal(a, b) for a, b in zip(sel, sel0)):
             return None
-        img = O.render_image(gg, H, W, K=K, tile=T)
+        img = O.render_image(gg, H, W, K=K, tile=T, normalize=normalize)
         return float((img * gout).sum())
 
     checked = 0
@@ -345,6 +345,32 @@ def _fd_check(n, seed):
 @pytest.mark.parametrize("n,seed", [(1, 20), (3, 21)])
 def test_gradients_match_central_finite_differences(n, seed):
     assert _fd_check(n, seed) > 5 * (5 + n)
+
+
+@pytest.mark.parametrize("K,normalize", [(None, True), (3, False), (None, False)])
+def test_ablation_mode_gradients_match_finite_differences(K, normalize):
+    """All of S_j (K = infinity) and/or no normalisation (Eq. 4 over S_j)."""
+    assert _fd_check(3, 23, K=K, normalize=normalize) > 3 * 8
+
+
+def test_unnormalised_all_candidates_is_eq4_restricted_to_the_tile():
+    """K = infinity without normalisation is Eq. 4 summed over S_j only."""
+    H, W = 40, 40
+    g = rand_set(30, 2, 24, s_range=(1.0, 4.0))
+    pts = O.pixel_centres(synth.sample_pixels(100, H, W, 3))
+    got = O.render_points(g, pts, H, W, K=None, normalize=False)
+    for (x, y), row in zip(pts, got):
+        mem = O.tile_members(g, int(x // 16), int(y // 16), 16, H, W)
+        want = np.zeros(2)
+        for i in np.nonzero(mem)[0]:
+            th = float(g.theta[i])
+            u = np.array([math.cos(th), math.sin(th)])
+            v = np.array([-math.sin(th), math.cos(th)])
+            d = np.array([x - float(np.float32(g.xy[i, 0] * np.float32(W))),
+                          y - float(np.float32(g.xy[i, 1] * np.float32(H)))])
+            q = (float(g.inv_scale[i, 0]) * (u @ d)) ** 2 + (float(g.inv_scale[i, 1]) * (v @ d)) ** 2
+            want += math.exp(-0.5 * q) * g.color[i].astype(np.float64)
+        np.testing.assert_allclose(row, want, rtol=1e-12, atol=1e-14)
 
 
 def test_colour_gradient_is_exact_weight_sum():
