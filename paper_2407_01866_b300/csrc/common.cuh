@@ -76,24 +76,21 @@ __device__ __forceinline__ float rank_key(float px, float py, float mx, float my
 }
 
 // Sorted insertion of (q, id) into ascending tq[0..K-1] / tid[0..K-1],
-// dropping the largest. Equal keys keep the earlier entry first, so feeding
-// candidates in ascending index order breaks ties toward the smaller index.
-// The K compares are independent; each slot then takes one of three values.
+// dropping the largest: the candidate bubbles down the list, swapping with
+// every entry whose key is larger. Equal keys keep the earlier entry first, so
+// feeding candidates in ascending index order breaks ties toward the smaller
+// index.
 template <int K>
 __device__ __forceinline__ void topk_insert(float (&tq)[K], int (&tid)[K], float q, int id) {
-  bool b[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k) b[k] = q < tq[k];
-#pragma unroll
-  for (int k = K - 1; k >= 1; --k) {
-    const float nq = b[k - 1] ? tq[k - 1] : (b[k] ? q : tq[k]);
-    const int ni = b[k - 1] ? tid[k - 1] : (b[k] ? id : tid[k]);
-    tq[k] = nq;
-    tid[k] = ni;
-  }
-  if (b[0]) {
-    tq[0] = q;
-    tid[0] = id;
+  for (int k = 0; k < K; ++k) {
+    const float oq = tq[k];
+    const int oi = tid[k];
+    const bool sw = q < oq;
+    tq[k] = sw ? q : oq;
+    tid[k] = sw ? id : oi;
+    q = sw ? oq : q;
+    id = sw ? oi : id;
   }
 }
 
