@@ -4,24 +4,42 @@
 // instantiate and dispatch them.
 //
 // One CTA renders one logical tile of TILE x TILE pixels, one pixel per
-// thread; each warp owns a compact 8 x 4 block so that its pixels share
-// most of their winners. The tile's list S_j (ascending Gaussian index) is
-// staged through shared memory in chunks of TILE*TILE records.
+// thread; each warp owns a compact 8 x 4 block of pixels.
+//
+// Fast path (the tile's list S_j fits one stage of CH records, the common
+// case): the list is staged once into shared memory, ordered by each
+// candidate's ranking key at the tile centre, nearest first. The order
+// decides only how much work is skipped, never which Gaussians win.
 //
 //   pass A  keys only: every pixel keeps its K smallest ranking keys q with a
 //           min/max insertion network, run only when some lane of the warp
-//           improves on its K-th key (warp vote). Gives q_min and the
-//           threshold tau = K-th smallest key.
-//   pass B  list order: a candidate is a winner iff q < tau, or q == tau
-//           while equal-key slots remain (K minus the keys below tau), which
-//           is exactly the top-K of the (q, index) order. Winners are blended
-//           with w = exp(-(q - q_min)/2) (Eq. 5).
-//   pass C  (adjoint only) candidate-major: threads own (candidate, group of
-//           pixels), re-test membership exactly from each pixel's (tau,
-//           position of its last tau-valued winner), and accumulate dL/dq
-//           moments in registers; one reduction and 5+n global atomics per
-//           (tile, Gaussian). Nothing is stored between forward and adjoint.
+//           improves on its K-th key (warp vote). Before 32 candidates are
+//           evaluated per pixel, the warp tests them lane-parallel against a
+//           lower bound of q over its 8 x 4 block: a candidate whose bound
+//           exceeds the K-th key of every pixel of the block cannot enter any
+//           top K and is skipped. Gives q_min, the K-th key tau and the
+//           smallest key left out of the top K.
+//   pass B  membership and blend: a candidate wins iff q < tau, or q == tau
+//           and its index is at most the pixel's tie cut-off (no limit unless
+//           a key equal to tau was left out; then the cut-off admits the
+//           smallest indices, as the (q, index) order of the top-K demands).
+//           Candidates are culled against the block's largest tau. Winners
+//           are blended with w = exp(-(q - q_min)/2) (Eq. 5); the adjoint
+//           records the ballot of winning pixels per (warp, candidate).
+//   pass C  (adjoint only) the winning (candidate, pixel) pairs are split
+//           evenly over the CTA's threads; each accumulates dL/dq moments in
+//           registers and leaves one partial sum per candidate it touched in
+//           a shared-memory slot with a single writer; one thread per
+//           candidate adds its slots and turns them into parameter gradients
+//           with 5+n global atomics.
+//
+// Longer lists take the chunked path: passes A and B stream the list in
+// ascending index order (equal keys at tau are admitted in that order), and
+// pass C re-tests membership per (candidate, pixel).
+// Nothing is stored between forward and adjoint.
 #pragma once
+#include <type_traits>
+
 #include "internal.h"
 
 namespace igs {
@@ -45,34 +63,137 @@ __device__ __forceinline__ int2 pixel_of(int t) {
   return make_int2((w % BPR) * 8 + (lane & 7), (w / BPR) * 4 + (lane >> 3));
 }
 
-constexpr float F_INF = __builtin_huge_valf();
+// Pixel centres of the calling warp's 8 x 4 block: (x_lo, x_hi, y_lo, y_hi).
+template <int TILE>
+__device__ __forceinline__ float4 block_rect(int x0, int y0) {
+  constexpr int BPR = TILE / 8;
+  const int w = threadIdx.x >> 5;
+  const float bx = (float)(x0 + (w % BPR) * 8) + 0.5f;
+  const float by = (float)(y0 + (w / BPR) * 4) + 0.5f;
+  return make_float4(bx, bx + 7.0f, by, by + 3.0f);
+}
 
-// Stage list entries [base, base+cnt) of the tile: geometry and index.
-// Colours of staged candidates live in shared memory, channel-major
-// s_col[c * NT + j], when the channel count is a compile-time constant.
+constexpr float F_INF = __builtin_huge_valf();
+constexpr int GID_NONE = 0x7fffffff;  // tie cut-off that admits every index
+
+// Staged candidate record in shared memory:
+//   a = (mx, my, A00, B)   geometry of the ranking key
+//   b = (A11, index as int bits)
+//   e = (ex, ey) = (det/A11, det/A00) with det = A00 A11 - B^2/4 = (t1 t2)^2,
+//       so that q >= ex dx^2 and q >= ey dy^2 for every displacement
+//       (fast path only).
+
+// Lower bound of the ranking key of staged record (a, a11, e) at every pixel
+// centre of rectangle R, valid for the float32 evaluation of rank_key: the
+// axis-wise bounds over the rectangle, reduced by a relative 1e-5 and by
+// 2e-6 times the largest sum of term magnitudes |A00| dx^2 + |B dx dy| +
+// A11 dy^2 over R (float32 rounding of the key, of the staged conic and of
+// this bound are each a few 2^-24 of those).
+__device__ __forceinline__ float key_lower_bound(const float4& a, float a11, const float2& e,
+                                                 const float4& R) {
+  const float ddx = fmaxf(fmaxf(R.x - a.x, a.x - R.y), 0.0f);
+  const float ddy = fmaxf(fmaxf(R.z - a.y, a.y - R.w), 0.0f);
+  const float L = fmaxf(ddx * ddx * e.x, ddy * ddy * e.y);
+  const float fx = fmaxf(fabsf(R.x - a.x), fabsf(R.y - a.x));
+  const float fy = fmaxf(fabsf(R.z - a.y), fabsf(R.w - a.y));
+  const float hb = 0.5f * fabsf(a.w);
+  const float M = (fabsf(a.z) + hb) * fx * fx + (a11 + hb) * fy * fy;
+  return fmaf(L, 1.0f - 1e-5f, -2e-6f * M);
+}
+
+// Largest value of v over the warp for non-negative keys (negative rounding
+// residues count as 0, which only loosens a cull threshold).
+__device__ __forceinline__ float warp_max_key(float v) {
+  return __uint_as_float(__reduce_max_sync(FULL_MASK, __float_as_uint(fmaxf(v, 0.0f))));
+}
+
+// Chunked path: stage list entries [base, base+cnt) in list order. Colours
+// of staged candidates live in shared memory, channel-major s_col[c * NT + j],
+// when the channel count is a compile-time constant.
 template <int NT, int NC>
 __device__ __forceinline__ void stage_chunk(const RenderParams& p, int base, int cnt,
-                                            float4* s_a, float* s_a11, int* s_gid,
-                                            float* s_col) {
-  if ((int)threadIdx.x < cnt) {
-    const int gid = p.list[base + threadIdx.x];
+                                            float4* s_a, float2* s_b, float* s_col) {
+  const int j = threadIdx.x;
+  if (j < cnt) {
+    const int gid = p.list[base + j];
     if ((unsigned)gid < (unsigned)p.N) {
       const GRec g = p.rec[gid];
-      s_a[threadIdx.x] = g.a;
-      s_a11[threadIdx.x] = g.b.x;
-      s_gid[threadIdx.x] = gid;
+      s_a[j] = g.a;
+      s_b[j] = make_float2(g.b.x, __int_as_float(gid));
       if (NC > 0) {
 #pragma unroll
         for (int c = 0; c < (NC > 0 ? NC : 1); ++c)
-          s_col[c * NT + threadIdx.x] = p.color[(int64_t)gid * NC + c];
+          s_col[c * NT + j] = p.color[(int64_t)gid * NC + c];
       }
     } else {  // corrupt list entry: a NaN key is never selected
-      s_a[threadIdx.x] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
-      s_a11[threadIdx.x] = 0.0f;
-      s_gid[threadIdx.x] = -1;
+      s_a[j] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+      s_b[j] = make_float2(0.f, __int_as_float(-1));
       if (NC > 0) {
 #pragma unroll
-        for (int c = 0; c < (NC > 0 ? NC : 1); ++c) s_col[c * NT + threadIdx.x] = 0.0f;
+        for (int c = 0; c < (NC > 0 ? NC : 1); ++c) s_col[c * NT + j] = 0.0f;
+      }
+      atomicOr(&p.status->flags, FLAG_INTERNAL);
+    }
+  }
+}
+
+// Fast path: stage the whole list (cnt <= NT <= blockDim.x), each record at
+// its rank in the order of the candidates' keys at (cx, cy) (ties, and the
+// low 8 bits of each key, broken by list position). s_key holds NT words
+// (16-byte aligned) of scratch that must not overlap the staged arrays.
+template <int NT, int NC>
+__device__ __forceinline__ void stage_sorted(const RenderParams& p, int base, int cnt, float cx,
+                                             float cy, float4* s_a, float2* s_b, float2* s_e,
+                                             float* s_col, unsigned* s_key) {
+  constexpr int NCS = NC > 0 ? NC : 1;
+  const int j = threadIdx.x;
+  GRec g;
+  float col[NCS];
+  int gid = -1;
+  unsigned key = 0xffffffffu;  // padding: never below a real key
+  if (j < cnt) {
+    const int e = p.list[base + j];
+    if ((unsigned)e < (unsigned)p.N) {
+      gid = e;
+      g = p.rec[gid];
+      if (NC > 0) {
+#pragma unroll
+        for (int c = 0; c < NCS; ++c) col[c] = p.color[(int64_t)gid * NC + c];
+      }
+      const float kc = fmaxf(rank_key(cx, cy, g.a.x, g.a.y, g.a.z, g.a.w, g.b.x), 0.0f);
+      key = (__float_as_uint(kc) & 0xffffff00u) | (unsigned)j;
+    } else {
+      key = 0xffffff00u | (unsigned)j;
+    }
+  }
+  const int cnt4 = (cnt + 3) & ~3;
+  if (j < cnt4) s_key[j] = key;
+  __syncthreads();
+  if (j < cnt) {
+    int r = 0;
+    const uint4* k4 = reinterpret_cast<const uint4*>(s_key);
+    for (int i = 0; i < cnt4 / 4; ++i) {
+      const uint4 v = k4[i];
+      r += (v.x < key ? 1 : 0) + (v.y < key ? 1 : 0) + (v.z < key ? 1 : 0) +
+           (v.w < key ? 1 : 0);
+    }
+    if (gid >= 0) {
+      const float d = g.b.z * g.b.w;
+      const float det = d * d;
+      s_a[r] = g.a;
+      s_b[r] = make_float2(g.b.x, __int_as_float(gid));
+      s_e[r] = make_float2(det / g.b.x, det / g.a.z);
+      if (NC > 0) {
+#pragma unroll
+        for (int c = 0; c < NCS; ++c) s_col[c * NT + r] = col[c];
+      }
+    } else {  // corrupt list entry: a NaN key is never selected
+      s_a[r] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+      s_b[r] = make_float2(0.f, __int_as_float(-1));
+      s_e[r] = make_float2(0.f, 0.f);
+      if (NC > 0) {
+#pragma unroll
+        for (int c = 0; c < NCS; ++c) s_col[c * NT + r] = 0.0f;
       }
       atomicOr(&p.status->flags, FLAG_INTERNAL);
     }
@@ -82,44 +203,20 @@ __device__ __forceinline__ void stage_chunk(const RenderParams& p, int base, int
 // Channel c of staged candidate j (shared memory if staged, else global).
 template <int NT, int NC>
 __device__ __forceinline__ float staged_colour(const RenderParams& p, const float* s_col,
-                                               const int* s_gid, int j, int c) {
+                                               const float2* s_b, int j, int c) {
   if (NC > 0) return s_col[c * NT + j];
-  return p.color[(int64_t)s_gid[j] * p.n + c];
+  return p.color[(int64_t)__float_as_int(s_b[j].y) * p.n + c];
 }
 
-// Pass A: the K smallest keys at (px, py), ascending. CH list entries are
-// staged per round ("Gaussians per stage", CH <= TILE*TILE).
-template <int TILE, int K, int CH>
-__device__ __forceinline__ void select_keys(const RenderParams& p, int2 range, float px,
-                                            float py, float (&tq)[KS<K>::A], float4* s_a,
-                                            float* s_a11, int* s_gid) {
+// Sorted insertion of key x into tq[0..A-1] (ascending), the largest key
+// dropping out into x. +inf inserts nothing.
+template <int A>
+__device__ __forceinline__ void insert_key(float (&tq)[A], float& x) {
 #pragma unroll
-  for (int k = 0; k < KS<K>::A; ++k) tq[k] = F_INF;
-  if (K == 0 && !p.normalize) return;  // every candidate wins, no shift needed
-  for (int base = range.x; base < range.y; base += CH) {
-    const int cnt = min(CH, range.y - base);
-    __syncthreads();
-    stage_chunk<CH, 0>(p, base, cnt, s_a, s_a11, s_gid, nullptr);
-    __syncthreads();
-#pragma unroll 4
-    for (int j = 0; j < cnt; ++j) {
-      const float4 a = s_a[j];
-      const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_a11[j]);
-      if (K == 0) {  // all of S_j: only the smallest key is needed
-        tq[0] = fminf(tq[0], q);
-        continue;
-      }
-      const bool better = q < tq[KS<K>::A - 1];
-      if (__any_sync(FULL_MASK, better)) {
-        float x = better ? q : F_INF;  // +inf (and NaN) insert nothing
-#pragma unroll
-        for (int k = 0; k < KS<K>::A; ++k) {
-          const float lo = fminf(tq[k], x);
-          x = fmaxf(tq[k], x);
-          tq[k] = lo;
-        }
-      }
-    }
+  for (int k = 0; k < A; ++k) {
+    const float lo = fminf(tq[k], x);
+    x = fmaxf(tq[k], x);
+    tq[k] = lo;
   }
 }
 
@@ -129,16 +226,50 @@ struct PixelBlend {
   float Z;          // sum of winner weights (0 if the pixel has none)
   float cr[NCR];    // blended colour
   float tau;        // K-th key (+inf if |S_j| < K)
-  float q0;         // smallest key
-  int posK;         // list position of the last tau-valued winner
+  float q0;         // smallest key (0 when unnormalised)
+  int gcut;         // largest index admitted among winners whose key equals tau
 };
 
-// Pass B: exact top-K membership in list order and the blend of Eq. 5.
+// ---------------------------------------------------------------------------
+// Chunked path (lists longer than one stage), list order.
+// ---------------------------------------------------------------------------
+
+// Pass A: the K smallest keys at (px, py), ascending.
+template <int TILE, int K, int CH>
+__device__ __forceinline__ void select_keys(const RenderParams& p, int2 range, float px,
+                                            float py, float (&tq)[KS<K>::A], float4* s_a,
+                                            float2* s_b) {
+#pragma unroll
+  for (int k = 0; k < KS<K>::A; ++k) tq[k] = F_INF;
+  if (K == 0 && !p.normalize) return;  // every candidate wins, no shift needed
+  for (int base = range.x; base < range.y; base += CH) {
+    const int cnt = min(CH, range.y - base);
+    __syncthreads();
+    stage_chunk<CH, 0>(p, base, cnt, s_a, s_b, nullptr);
+    __syncthreads();
+#pragma unroll 4
+    for (int j = 0; j < cnt; ++j) {
+      const float4 a = s_a[j];
+      const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_b[j].x);
+      if (K == 0) {  // all of S_j: only the smallest key is needed
+        tq[0] = fminf(tq[0], q);
+        continue;
+      }
+      const bool better = q < tq[KS<K>::A - 1];
+      if (__any_sync(FULL_MASK, better)) {
+        float x = better ? q : F_INF;  // +inf (and NaN) insert nothing
+        insert_key<KS<K>::A>(tq, x);
+      }
+    }
+  }
+}
+
+// Pass B: exact top-K membership in list (index) order and the blend of Eq. 5.
 template <int TILE, int K, int NC, int CH>
 __device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, float px,
                                            float py, const float (&tq)[KS<K>::A],
                                            PixelBlend<Chan<NC>::R>& r, float4* s_a,
-                                           float* s_a11, int* s_gid, float* s_col) {
+                                           float2* s_b, float* s_col) {
   constexpr int NCR = Chan<NC>::R;
   const int n = nchan<NC>(p);
   r.q0 = p.normalize ? tq[0] : 0.0f;  // unnormalised: w = exp(-q/2) itself
@@ -147,25 +278,24 @@ __device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, fl
 #pragma unroll
   for (int k = 0; k < KS<K>::A; ++k) lt += tq[k] < r.tau ? 1 : 0;
   int eq_left = K - lt;  // tau-valued slots still open
-  r.posK = -1;
+  r.gcut = -1;
   r.Z = 0.0f;
 #pragma unroll
   for (int c = 0; c < NCR; ++c) r.cr[c] = 0.0f;
   for (int base = range.x; base < range.y; base += CH) {
     const int cnt = min(CH, range.y - base);
     __syncthreads();
-    stage_chunk<CH, NC>(p, base, cnt, s_a, s_a11, s_gid, s_col);
+    stage_chunk<CH, NC>(p, base, cnt, s_a, s_b, s_col);
     __syncthreads();
-    const int rel = base - range.x;
 #pragma unroll 2
     for (int j = 0; j < cnt; ++j) {
       const float4 a = s_a[j];
-      const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_a11[j]);
+      const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_b[j].x);
       bool win = q < r.tau;
       if (q == r.tau && eq_left > 0) {
         win = true;
         --eq_left;
-        r.posK = rel + j;
+        r.gcut = __float_as_int(s_b[j].y);
       }
       if (__any_sync(FULL_MASK, win)) {
         if (win) {
@@ -174,7 +304,7 @@ __device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, fl
 #pragma unroll
           for (int c = 0; c < NCR; ++c)
             if (NC > 0 || c < n)
-              r.cr[c] = fmaf(w, staged_colour<CH, NC>(p, s_col, s_gid, j, c), r.cr[c]);
+              r.cr[c] = fmaf(w, staged_colour<CH, NC>(p, s_col, s_b, j, c), r.cr[c]);
         }
       }
     }
@@ -185,82 +315,129 @@ __device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, fl
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint fast path for tiles whose whole list fits one stage (the common
-// case): the list is staged once, passes A and B run warp-locally over it in
-// list order, and pass B's ballots record, per (warp block, candidate), the
-// mask of pixels where the candidate is a winner. Pass C then walks only the
-// winning (candidate, pixel) pairs, split evenly over the CTA's threads.
+// Fast path: one staged, key-ordered list; per-warp culling.
 // ---------------------------------------------------------------------------
 
-// Pass A over the staged list (list order, keys only).
+// Pass A over the staged list. mdrop receives the smallest evaluated key
+// that did not stay in the top K (+inf if none): a key equal to tau left out.
 template <int K>
-__device__ __forceinline__ void staged_keys(const RenderParams& p, int cnt, float px, float py,
-                                            const float4* s_a, const float* s_a11,
-                                            float (&tq)[KS<K>::A]) {
+__device__ __forceinline__ void culled_keys(const RenderParams& p, int cnt, float px, float py,
+                                            bool live, const float4& R, const float4* s_a,
+                                            const float2* s_b, const float2* s_e,
+                                            float (&tq)[KS<K>::A], float& mdrop) {
+  constexpr int A = KS<K>::A;
 #pragma unroll
-  for (int k = 0; k < KS<K>::A; ++k) tq[k] = F_INF;
+  for (int k = 0; k < A; ++k) tq[k] = F_INF;
+  mdrop = F_INF;
   if (K == 0 && !p.normalize) return;
-#pragma unroll 4
-  for (int j = 0; j < cnt; ++j) {
-    const float4 a = s_a[j];
-    const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_a11[j]);
-    if (K == 0) {
-      tq[0] = fminf(tq[0], q);
-      continue;
-    }
-    const bool better = q < tq[KS<K>::A - 1];
-    if (__any_sync(FULL_MASK, better)) {
-      float x = better ? q : F_INF;
-#pragma unroll
-      for (int k = 0; k < KS<K>::A; ++k) {
-        const float lo = fminf(tq[k], x);
-        x = fmaxf(tq[k], x);
-        tq[k] = lo;
+  const int lane = threadIdx.x & 31;
+  float thr = F_INF;  // no lane of the block can use a key above this
+  // a first group of 16 gives every lane K keys early (nearest first)
+  for (int c0 = 0, gw = 16; c0 < cnt; c0 += gw, gw = 32) {
+    const int jl = c0 + lane;
+    const bool surv =
+        lane < gw && jl < cnt && !(key_lower_bound(s_a[jl], s_b[jl].x, s_e[jl], R) > thr);
+    unsigned m = __ballot_sync(FULL_MASK, surv);
+    while (m) {
+      const int j = c0 + __ffs(m) - 1;
+      m &= m - 1;
+      const float4 a = s_a[j];
+      const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_b[j].x);
+      if (K == 0) {  // all of S_j: only the smallest key is needed
+        tq[0] = fminf(tq[0], q);
+        continue;
       }
+      const bool better = q < tq[A - 1];
+      float out = q;
+      if (__any_sync(FULL_MASK, better)) {
+        float x = better ? q : F_INF;
+        insert_key<A>(tq, x);
+        out = better ? x : q;
+      }
+      mdrop = fminf(mdrop, out);
     }
+    thr = warp_max_key(live ? tq[A - 1] : 0.0f);
   }
 }
 
-// Pass B over the staged list: exact (q, index) membership, blend, and the
-// ballot of winning live pixels of this warp per candidate into mask_w[].
-template <int K, int NC, int CH>
-__device__ __forceinline__ void staged_blend(const RenderParams& p, int cnt, float px, float py,
-                                             bool live, const float (&tq)[KS<K>::A],
-                                             const float4* s_a, const float* s_a11,
-                                             const int* s_gid, const float* s_col,
+// Index cut-off of a pixel whose tau ties with a key left out: the eq_left-th
+// smallest index among candidates with key tau, eq_left = K minus the number
+// of keys below tau. Rare; every candidate is re-evaluated once per round.
+template <int K>
+__device__ __forceinline__ int tie_cutoff(int cnt, float px, float py, bool tie, float tau,
+                                          const float (&tq)[KS<K>::A], const float4* s_a,
+                                          const float2* s_b) {
+  int lt = 0;
+#pragma unroll
+  for (int k = 0; k < KS<K>::A; ++k) lt += tq[k] < tau ? 1 : 0;
+  const int eq_left = K - lt;
+  int gc = -1;
+  for (int round = 0;; ++round) {
+    const bool need = tie && round < eq_left;
+    if (!__any_sync(FULL_MASK, need)) break;
+    int gmin = GID_NONE;
+    for (int j = 0; j < cnt; ++j) {
+      const float4 a = s_a[j];
+      const float2 b = s_b[j];
+      const float q = rank_key(px, py, a.x, a.y, a.z, a.w, b.x);
+      const int gid = __float_as_int(b.y);
+      if (need && q == tau && gid > gc && gid < gmin) gmin = gid;
+    }
+    if (need) gc = gmin;
+  }
+  return tie ? gc : GID_NONE;
+}
+
+// Pass B over the staged list: membership, blend, and (MASKS) the ballot of
+// winning live pixels of this warp per candidate into mask_w[].
+template <int K, int NC, int CH, bool MASKS>
+__device__ __forceinline__ void culled_blend(const RenderParams& p, int cnt, float px, float py,
+                                             bool live, const float4& R,
+                                             const float (&tq)[KS<K>::A], float mdrop,
+                                             const float4* s_a, const float2* s_b,
+                                             const float2* s_e, const float* s_col,
                                              unsigned* mask_w, PixelBlend<Chan<NC>::R>& r) {
   constexpr int NCR = Chan<NC>::R;
+  constexpr int A = KS<K>::A;
   const int n = nchan<NC>(p);
   const int lane = threadIdx.x & 31;
   r.q0 = p.normalize ? tq[0] : 0.0f;
-  r.tau = K == 0 ? F_INF : tq[KS<K>::A - 1];
-  r.posK = -1;
+  r.tau = K == 0 ? F_INF : tq[A - 1];
+  r.gcut = GID_NONE;
+  if (K > 0) {
+    const bool tie = mdrop == r.tau && r.tau < F_INF;
+    if (__any_sync(FULL_MASK, tie))
+      r.gcut = tie_cutoff<K>(cnt, px, py, tie, r.tau, tq, s_a, s_b);
+  }
   r.Z = 0.0f;
 #pragma unroll
   for (int c = 0; c < NCR; ++c) r.cr[c] = 0.0f;
-  int lt = 0;
+  const float T = K == 0 ? F_INF : warp_max_key(live ? r.tau : 0.0f);
+  for (int c0 = 0; c0 < cnt; c0 += 32) {
+    const int jl = c0 + lane;
+    const bool in = jl < cnt;
+    const bool surv = in && !(key_lower_bound(s_a[jl], s_b[jl].x, s_e[jl], R) > T);
+    if (MASKS && in && !surv) mask_w[jl] = 0u;
+    unsigned m = __ballot_sync(FULL_MASK, surv);
+    while (m) {
+      const int j = c0 + __ffs(m) - 1;
+      m &= m - 1;
+      const float4 a = s_a[j];
+      const float2 b = s_b[j];
+      const float q = rank_key(px, py, a.x, a.y, a.z, a.w, b.x);
+      const bool win = q < r.tau || (q == r.tau && __float_as_int(b.y) <= r.gcut);
+      if (MASKS) {
+        const unsigned bal = __ballot_sync(FULL_MASK, win && live);
+        if (lane == 0) mask_w[j] = bal;
+      }
+      if (win) {
+        const float w = blend_weight(r.q0, q);  // exactly 1 at q = q_min
+        r.Z += w;
 #pragma unroll
-  for (int k = 0; k < KS<K>::A; ++k) lt += tq[k] < r.tau ? 1 : 0;
-  int eq_left = K - lt;
-#pragma unroll 2
-  for (int j = 0; j < cnt; ++j) {
-    const float4 a = s_a[j];
-    const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_a11[j]);
-    bool win = q < r.tau;
-    if (q == r.tau && eq_left > 0) {
-      win = true;
-      --eq_left;
-      r.posK = j;
-    }
-    const unsigned bal = __ballot_sync(FULL_MASK, win && live);
-    if (lane == 0) mask_w[j] = bal;
-    if (win) {
-      const float w = blend_weight(r.q0, q);
-      r.Z += w;
-#pragma unroll
-      for (int c = 0; c < NCR; ++c)
-        if (NC > 0 || c < n)
-          r.cr[c] = fmaf(w, staged_colour<CH, NC>(p, s_col, s_gid, j, c), r.cr[c]);
+        for (int c = 0; c < NCR; ++c)
+          if (NC > 0 || c < n)
+            r.cr[c] = fmaf(w, staged_colour<CH, NC>(p, s_col, s_b, j, c), r.cr[c]);
+      }
     }
   }
   const float iz = p.normalize ? (r.Z > 0.0f ? 1.0f / r.Z : 0.0f) : 1.0f;
@@ -272,20 +449,34 @@ template <int TILE, int K, int NC>
 __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(RenderParams p) {
   constexpr int NT = TILE * TILE;
   __shared__ float4 s_a[NT];
-  __shared__ float s_a11[NT];
-  __shared__ int s_gid[NT];
+  __shared__ float2 s_b[NT];
+  __shared__ float2 s_e[NT];
+  __shared__ __align__(16) unsigned s_key[NT];
   __shared__ float s_col[NT * (NC > 0 ? NC : 1)];
   const int tile_id = blockIdx.x;
-  const int tx = tile_id % p.tiles_x, ty = tile_id / p.tiles_x;
+  const int x0 = (tile_id % p.tiles_x) * TILE, y0 = (tile_id / p.tiles_x) * TILE;
   const int2 lp = pixel_of<TILE>(threadIdx.x);
-  const int x = tx * TILE + lp.x, y = ty * TILE + lp.y;
+  const int x = x0 + lp.x, y = y0 + lp.y;
   const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+  const bool in_img = x < p.W && y < p.H;
   const int2 range = p.range[tile_id];
+  const int len = range.y - range.x;
   float tq[KS<K>::A];
-  select_keys<TILE, K, NT>(p, range, px, py, tq, s_a, s_a11, s_gid);
   PixelBlend<Chan<NC>::R> r;
-  blend_pass<TILE, K, NC, NT>(p, range, px, py, tq, r, s_a, s_a11, s_gid, s_col);
-  if (x >= p.W || y >= p.H) return;
+  if (len <= NT) {
+    stage_sorted<NT, NC>(p, range.x, len, (float)x0 + 0.5f * TILE, (float)y0 + 0.5f * TILE,
+                         s_a, s_b, s_e, s_col, s_key);
+    __syncthreads();
+    const float4 R = block_rect<TILE>(x0, y0);
+    float mdrop;
+    culled_keys<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tq, mdrop);
+    culled_blend<K, NC, NT, false>(p, len, px, py, in_img, R, tq, mdrop, s_a, s_b, s_e, s_col,
+                                   nullptr, r);
+  } else {
+    select_keys<TILE, K, NT>(p, range, px, py, tq, s_a, s_b);
+    blend_pass<TILE, K, NC, NT>(p, range, px, py, tq, r, s_a, s_b, s_col);
+  }
+  if (!in_img) return;
   const int n = nchan<NC>(p);
   const int64_t plane = (int64_t)p.H * p.W;
   const int64_t o = (int64_t)y * p.W + x;
@@ -305,28 +496,28 @@ struct TileCtx {
 };
 
 // Dynamic shared-memory layout of the adjoint kernel (in 4-byte words), for
-// NT pixels, n channels and CH Gaussians per stage.
+// NT pixels, n channels and CH Gaussians per stage (64 <= CH <= NT).
 struct BwdSmem {
-  int a, a11, gid, col, ps0, ps1, gh, part, slotj, loss, scan, start, mask, off, total;
+  int a, b, col, ps0, gh, slot_a, slot_b, mask, coff, start, loss, scan, total;
 };
 __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   const int NWB = NT / 32;
+  const int np = 5 + n;
+  auto al4 = [](int v) { return (v + 3) & ~3; };
   BwdSmem L;
   int o = 0;
-  L.a = o;     o += 4 * NT;            // float4 staged geometry
-  L.a11 = o;   o += NT;
-  L.gid = o;   o += NT;
-  L.col = o;   o += n * CH;            // staged colours, channel-major
-  L.ps0 = o;   o += 4 * NT;            // float4 (px, py, tau, q0)
-  L.ps1 = o;   o += 2 * NT;            // float2 (posK bits, beta)
-  L.gh = o;    o += n * NT;            // per-pixel -g/(2Z), channel-major
-  L.part = o;  o += 2 * (5 + n) * NT;  // pass C partial sums (two slots per thread)
-  L.slotj = o; o += 2 * NT;            // candidate held by each slot
-  L.loss = o;  o += 2 * (NT / 32) + 2; // doubles
-  L.scan = o;  o += 34;                // integer block-scan scratch
-  L.start = o; o += NT / 2;            // shorts: item where each thread's pair range starts
-  L.mask = o;  o += NWB * CH;          // winner masks [warp block][candidate]
-  L.off = o;   o += (NWB * CH + 2) / 2;  // shorts: pair offsets of (candidate, block) items
+  L.a = o;      o += 4 * CH;              // float4 (mx, my, A00, B)
+  L.b = o;      o += 2 * CH;              // float2 (A11, index)
+  L.col = o;    o = al4(o + n * CH);      // staged colours, channel-major
+  L.ps0 = o;    o += 4 * NT;              // float4 (px, py, q0, beta) per pixel
+  L.gh = o;     o = al4(o + n * NT);      // per-pixel -g/(2Z), channel-major
+  L.slot_a = o; o = al4(o + np * CH);     // pass C per-candidate sums; (ex, ey) before
+  L.slot_b = o; o = al4(o + np * NT);     // pass C per-thread sums; rank keys before
+  L.mask = o;   o += (NWB * CH > 2 * NT ? NWB * CH : 2 * NT);  // ballots; chunked (tau, cut)
+  L.coff = o;   o += CH + 1;              // first pair of every candidate
+  L.start = o;  o += (NT + 1) / 2;        // shorts: item where each thread's pairs start
+  L.loss = (o + 1) & ~1; o = L.loss + 2 * NWB + 2;  // doubles
+  L.scan = o;   o += 34;                  // integer block-scan scratch
   L.total = o;
   return L;
 }
@@ -391,28 +582,52 @@ __device__ __forceinline__ int block_scan_int(int v, int* scratch, int& total) {
   return r;
 }
 
+// floor(a / d) for 0 <= a < 2^22 and d >= 1, given inv = 1/d in float32: the
+// float quotient is within one of the exact one, which the checks correct.
+__device__ __forceinline__ int div_small(int a, int d, float inv) {
+  int q = (int)((float)a * inv);
+  if (q * d > a) --q;
+  else if ((q + 1) * d <= a) ++q;
+  return q;
+}
+
+// Position of the k-th (0-based) set bit of m, for k < popc(m).
+__device__ __forceinline__ int nth_set_bit(unsigned m, int k) {
+  int pos = 0;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const int c = __popc(m & ((1u << s) - 1u));
+    const bool up = k >= c;
+    k = up ? k - c : k;
+    m = up ? m >> s : m;
+    pos = up ? pos + s : pos;
+  }
+  return pos;
+}
+
 // Pass C of the fast path. The winning (candidate, pixel) pairs, in
 // (candidate, warp block, pixel) order, are split into equal contiguous
-// ranges, one per thread. A thread accumulates the candidates of its range
-// in registers; a candidate whose pairs all lie inside one range is finished
-// by that thread, the first and last candidates of every range go to two
-// slots, and each candidate's owner thread adds up the slots that hold it.
+// ranges, one per thread; a thread accumulates the candidates of its range
+// in registers. A candidate's partial sums go to the candidate's slot A_j,
+// written by the one thread whose range holds the candidate's first pair,
+// or, for the candidate a range opens with when it began in an earlier
+// range, to that thread's slot B_t. After a barrier, the thread of candidate
+// j adds A_j and the B_t of the later threads its pairs reach, and turns the
+// sums into parameter gradients.
 template <int TILE, int NC, int CH>
 __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx& t, int cnt,
-                                            const float4* s_a, const float* s_a11,
-                                            const int* s_gid, const float* s_col,
-                                            const unsigned* s_mask, const float4* s_ps0,
-                                            const float2* s_ps1, const float* s_gh,
-                                            float* s_slot, int* s_slotj, short* s_off,
+                                            const float4* s_a, const float2* s_b,
+                                            const float* s_col, const unsigned* s_mask,
+                                            const float4* s_ps0, const float* s_gh,
+                                            float* s_slot_a, float* s_slot_b, int* s_coff,
                                             int* s_scan, short* s_start) {
   constexpr int NT = TILE * TILE;
   constexpr int NWB = NT / 32;
   constexpr int NCR = Chan<NC>::R;
   const int n = nchan<NC>(p);
-  const int np = 5 + n;
   const int nit = cnt * NWB;
   auto mask_of = [&](int it) { return s_mask[(it % NWB) * CH + it / NWB]; };
-  // exclusive offsets of the items' pair counts
+  // pair offsets of the items (candidate-major), and where each range starts
   const int per_it = (nit + NT - 1) / NT;
   const int i0 = (int)threadIdx.x * per_it;
   int loc = 0;
@@ -421,77 +636,79 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
   int P;
   int run = block_scan_int(loc, s_scan, P);
   const int per = (P + NT - 1) / NT;  // pairs per thread
-  for (int k = 0; k < per_it; ++k)
-    if (i0 + k < nit) {
-      const int c = __popc(mask_of(i0 + k));
-      s_off[i0 + k] = (short)run;
-      // the threads whose range starts inside this item begin here
-      for (int th = (run + per - 1) / max(per, 1); per > 0 && th * per < run + c; ++th)
-        s_start[th] = i0 + k;
+  const float inv_per = per > 0 ? 1.0f / (float)per : 0.0f;
+  for (int k = 0; k < per_it; ++k) {
+    const int it = i0 + k;
+    if (it < nit) {
+      const int c = __popc(mask_of(it));
+      if (it % NWB == 0) s_coff[it / NWB] = run;
+      if (c > 0) {  // ranges starting at pairs run .. run+c-1
+        const int th0 = div_small(run + per - 1, per, inv_per);
+        const int th1 = div_small(run + c - 1, per, inv_per);
+        for (int th = th0; th <= th1; ++th) s_start[th] = (short)it;
+      }
       run += c;
     }
-  if (threadIdx.x == 0) s_off[nit] = (short)P;  // P <= pixels * K <= 4096
-  s_slotj[2 * threadIdx.x] = -1;
-  s_slotj[2 * threadIdx.x + 1] = -1;
+  }
+  if (threadIdx.x == 0) s_coff[cnt] = P;
   __syncthreads();
 
   const int r0 = (int)threadIdx.x * per;
   const int r1 = min(P, r0 + per);
   if (r0 < r1) {
     int it = s_start[threadIdx.x];
-    const int j_first = it / NWB;
+    int j = it / NWB, wb = it - j * NWB;
+    int ioff = s_coff[j];
+    for (int w2 = 0; w2 < wb; ++w2) ioff += __popc(s_mask[w2 * CH + j]);
     unsigned m = mask_of(it);
-    for (int k = r0 - s_off[it]; k > 0; --k) m &= m - 1;
-    int j = j_first, wb = it - j * NWB;
+    m &= 0xffffffffu << nth_set_bit(m, r0 - ioff);
+    const int j_first = j;
+    const bool cont = s_coff[j] < r0;  // the first candidate began in an earlier range
     float4 a = s_a[j];
-    float a11 = s_a11[j];
+    float a11 = s_b[j].x;
     float cc[NCR];
     auto load_colour = [&](int jj) {
 #pragma unroll
       for (int c = 0; c < NCR; ++c)
-        cc[c] = (NC > 0 || c < n) ? staged_colour<CH, NC>(p, s_col, s_gid, jj, c) : 0.0f;
+        cc[c] = (NC > 0 || c < n) ? staged_colour<CH, NC>(p, s_col, s_b, jj, c) : 0.0f;
     };
     load_colour(j);
     float T[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     float Tc[NCR];
 #pragma unroll
     for (int c = 0; c < NCR; ++c) Tc[c] = 0.0f;
-    // A candidate of a thread's range gets a slot if the range may not hold
-    // all of its pairs: the first one, and the one open when the range ends.
-    auto flush = [&](int jj, bool at_end) {
-      if (jj == j_first || at_end) {
-        const int slot = 2 * (int)threadIdx.x + (jj == j_first ? 0 : 1);
-        float* dst = s_slot + slot * np;
+    auto flush = [&](int jj) {
+      const bool to_b = cont && jj == j_first;
+      float* dst = to_b ? s_slot_b + threadIdx.x : s_slot_a + jj;
+      const int stride = to_b ? NT : CH;
 #pragma unroll
-        for (int k = 0; k < 5; ++k) dst[k] = T[k];
-#pragma unroll
-        for (int c = 0; c < NCR; ++c)
-          if (NC > 0 || c < n) dst[5 + c] = Tc[c];
-        s_slotj[slot] = jj;
-      } else {
-        const int gid = s_gid[jj];
-        if ((unsigned)gid < (unsigned)p.N) emit_grad<NC>(p, t, gid, T, Tc);
+      for (int k = 0; k < 5; ++k) {
+        dst[k * stride] = T[k];
+        T[k] = 0.0f;
       }
 #pragma unroll
-      for (int k = 0; k < 5; ++k) T[k] = 0.0f;
-#pragma unroll
-      for (int c = 0; c < NCR; ++c) Tc[c] = 0.0f;
+      for (int c = 0; c < NCR; ++c) {
+        if (NC > 0 || c < n) dst[(5 + c) * stride] = Tc[c];
+        Tc[c] = 0.0f;
+      }
     };
     for (int e = r0; e < r1; ++e) {
       const int i = wb * 32 + (__ffs(m) - 1);
       m &= m - 1;
-      const float4 s0 = s_ps0[i];
-      const float beta = s_ps1[i].y;
+      const float4 s0 = s_ps0[i];  // (px, py, q0, beta)
       // the ranking key of pass A, recomputed bit for bit (same sequence)
       const float dx = __fsub_rn(s0.x, a.x);
       const float dy = __fsub_rn(s0.y, a.y);
       const float h = __fmaf_rn(a.w, dy, __fmul_rn(a.z, dx));
       const float q = __fmaf_rn(h, dx, __fmul_rn(__fmul_rn(a11, dy), dy));
-      const float w = blend_weight(s0.w, q);
-      float gd = -beta;
+      const float w = blend_weight(s0.z, q);
+      float gh[NCR];
+      float gd = -s0.w;
 #pragma unroll
-      for (int c = 0; c < NCR; ++c)
-        if (NC > 0 || c < n) gd = fmaf(s_gh[c * NT + i], cc[c], gd);
+      for (int c = 0; c < NCR; ++c) {
+        gh[c] = (NC > 0 || c < n) ? s_gh[c * NT + i] : 0.0f;
+        if (NC > 0 || c < n) gd = fmaf(gh[c], cc[c], gd);
+      }
       const float Gq = w * gd;
       const float e1 = Gq * dx, e2 = Gq * dy;
       T[0] += e1;
@@ -501,7 +718,7 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
       T[4] = fmaf(e2, dy, T[4]);
 #pragma unroll
       for (int c = 0; c < NCR; ++c)
-        if (NC > 0 || c < n) Tc[c] = fmaf(w, s_gh[c * NT + i], Tc[c]);
+        if (NC > 0 || c < n) Tc[c] = fmaf(w, gh[c], Tc[c]);
       if (m == 0 && e + 1 < r1) {
         do {
           ++it;
@@ -510,134 +727,53 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
         const int nj = it / NWB;
         wb = it - nj * NWB;
         if (nj != j) {
-          flush(j, false);
+          flush(j);
           j = nj;
           a = s_a[j];
-          a11 = s_a11[j];
+          a11 = s_b[j].x;
           load_colour(j);
         }
       }
     }
-    flush(j, true);
+    flush(j);
   }
   __syncthreads();
   if ((int)threadIdx.x < cnt) {
     const int j = threadIdx.x;
-    const int e0 = s_off[j * NWB], e1 = s_off[(j + 1) * NWB];
+    const int e0 = s_coff[j], e1 = s_coff[j + 1];
     if (e1 > e0) {
-      float T[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      float T[5];
       float Tc[NCR];
 #pragma unroll
-      for (int c = 0; c < NCR; ++c) Tc[c] = 0.0f;
-      bool held = false;
-      for (int th = e0 / per; th <= (e1 - 1) / per; ++th) {
-        for (int sl = 0; sl < 2; ++sl) {
-          if (s_slotj[2 * th + sl] != j) continue;
-          held = true;
-          const float* src = s_slot + (2 * th + sl) * np;
+      for (int k = 0; k < 5; ++k) T[k] = s_slot_a[k * CH + j];
 #pragma unroll
-          for (int k = 0; k < 5; ++k) T[k] += src[k];
+      for (int c = 0; c < NCR; ++c)
+        Tc[c] = (NC > 0 || c < n) ? s_slot_a[(5 + c) * CH + j] : 0.0f;
+      const int th1 = div_small(e1 - 1, per, inv_per);
+      for (int th = div_small(e0, per, inv_per) + 1; th <= th1; ++th) {
 #pragma unroll
-          for (int c = 0; c < NCR; ++c)
-            if (NC > 0 || c < n) Tc[c] += src[5 + c];
-        }
+        for (int k = 0; k < 5; ++k) T[k] += s_slot_b[k * NT + th];
+#pragma unroll
+        for (int c = 0; c < NCR; ++c)
+          if (NC > 0 || c < n) Tc[c] += s_slot_b[(5 + c) * NT + th];
       }
-      const int gid = s_gid[j];
-      if (held && (unsigned)gid < (unsigned)p.N) emit_grad<NC>(p, t, gid, T, Tc);
+      const int gid = __float_as_int(s_b[j].y);
+      if ((unsigned)gid < (unsigned)p.N) emit_grad<NC>(p, t, gid, T, Tc);
     }
   }
 }
 
-// Adjoint of one tile: passes A and B per pixel, then pass C per candidate.
-template <int TILE, int K, int NC, int CH>
-__device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t, float* smem) {
+// Pass C of the chunked path: threads own (candidate, group of pixels) and
+// re-test membership from each pixel's (tau, tie cut-off).
+template <int TILE, int NC, int CH>
+__device__ __forceinline__ void chunked_pass_c(const RenderParams& p, const TileCtx& t,
+                                               const float4* s_ps0, const float2* s_ps1,
+                                               const float* s_gh, float* s_part) {
   constexpr int NT = TILE * TILE;
   constexpr int NCR = Chan<NC>::R;
   const int n = nchan<NC>(p);
-  constexpr int NWB = NT / 32;
-  const BwdSmem SL = bwd_smem(NT, n, CH);
-  float4* s_a = reinterpret_cast<float4*>(smem + SL.a);
-  float* s_a11 = smem + SL.a11;
-  int* s_gid = reinterpret_cast<int*>(smem + SL.gid);
-  float* s_col = smem + SL.col;
-  float4* s_ps0 = reinterpret_cast<float4*>(smem + SL.ps0);
-  float2* s_ps1 = reinterpret_cast<float2*>(smem + SL.ps1);
-  float* s_gh = smem + SL.gh;
-  float* s_part = smem + SL.part;
-  double* s_loss = reinterpret_cast<double*>(smem + SL.loss);
-  unsigned* s_mask = reinterpret_cast<unsigned*>(smem + SL.mask);
-  short* s_off = reinterpret_cast<short*>(smem + SL.off);
-  int* s_slotj = reinterpret_cast<int*>(smem + SL.slotj);
-
-  const int2 lp = pixel_of<TILE>(threadIdx.x);
-  const int x = t.x0 + lp.x, y = t.y0 + lp.y;
-  const float px = (float)x + 0.5f, py = (float)y + 0.5f;
-  const int2 range = t.range;
-
-  // ---- passes A and B: per-pixel forward values and upstream gradient
-  const int len = range.y - range.x;
-  const bool fast = len <= CH;
-  float tq[KS<K>::A];
-  PixelBlend<NCR> r;
-  if (fast) {
-    __syncthreads();  // the previous tile of a persistent CTA is done with smem
-    stage_chunk<CH, NC>(p, range.x, len, s_a, s_a11, s_gid, s_col);
-    __syncthreads();
-    const int w = threadIdx.x >> 5;
-    staged_keys<K>(p, len, px, py, s_a, s_a11, tq);
-    staged_blend<K, NC, CH>(p, len, px, py, x < t.W && y < t.H, tq, s_a, s_a11, s_gid, s_col,
-                            s_mask + w * CH, r);
-  } else {
-    select_keys<TILE, K, CH>(p, range, px, py, tq, s_a, s_a11, s_gid);
-    blend_pass<TILE, K, NC, CH>(p, range, px, py, tq, r, s_a, s_a11, s_gid, s_col);
-  }
-
-  float loss = 0.0f;
-  const bool live = x < t.W && y < t.H && r.Z > 0.0f;
-  float beta = 0.0f;
-  const float iz = live ? (p.normalize ? 1.0f / r.Z : 1.0f) : 0.0f;
-  const int64_t plane = (int64_t)t.H * t.W;
-  const int64_t o = t.off + (int64_t)y * t.W + x;
-#pragma unroll
-  for (int c = 0; c < NCR; ++c) {
-    if (NC > 0 || c < n) {
-      float g = 0.0f;
-      if (live) {
-        if (p.grad_img) {
-          g = p.grad_img[c * plane + o];
-        } else {
-          const float d = r.cr[c] - p.target[c * plane + o];
-          loss += fabsf(d);
-          g = sign_f(d) * t.inv_count;
-        }
-      }
-      const float gh = -0.5f * g * iz;  // dL/dq_k = w_k * (sum_c gh_c c_k,c - beta)
-      if (p.normalize) beta = fmaf(gh, r.cr[c], beta);
-      s_gh[c * NT + threadIdx.x] = gh;
-    }
-  }
-  s_ps0[threadIdx.x] = make_float4(px, py, live ? r.tau : -F_INF, r.q0);
-  s_ps1[threadIdx.x] = make_float2(__int_as_float(r.posK), beta);
-  if (!p.grad_img) {
-    const double l = warp_sum<double>((double)loss);
-    if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = l;
-  }
-  __syncthreads();
-  if (!p.grad_img && threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int i = 0; i < NT / 32; ++i) tot += s_loss[i];
-    if (tot != 0.0) atomicAdd(t.loss_acc, tot);
-  }
-
-  // ---- pass C: candidate-major accumulation of the adjoint
-  if (fast) {
-    flat_pass_c<TILE, NC, CH>(p, t, len, s_a, s_a11, s_gid, s_col, s_mask, s_ps0, s_ps1, s_gh,
-                              s_part,
-                              s_slotj, s_off, reinterpret_cast<int*>(smem + SL.scan),
-                              reinterpret_cast<short*>(smem + SL.start));
-    return;
-  }
   const int np = 5 + n;
+  const int2 range = t.range;
   for (int cbase = range.x; cbase < range.y; cbase += CH) {
     const int C = min(CH, range.y - cbase);
     const int G = max(1, NT / C);            // pixel groups per candidate
@@ -651,7 +787,6 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
     const int gid = p.list[cbase + j];
     const bool act = grp < G && (unsigned)gid < (unsigned)p.N;
     if (act) {
-      const int pos = cbase - range.x + j;
       const GRec rc = p.rec[gid];
       const float* col = p.color + (int64_t)gid * n;
       float cc[NCR];
@@ -666,10 +801,10 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
         const float dy = __fsub_rn(s0.y, rc.a.y);
         const float h = __fmaf_rn(rc.a.w, dy, __fmul_rn(rc.a.z, dx));
         const float q = __fmaf_rn(h, dx, __fmul_rn(__fmul_rn(rc.b.x, dy), dy));
-        const bool win = q < s0.z || (q == s0.z && pos <= __float_as_int(s1.x));
+        const bool win = q < s1.x || (q == s1.x && gid <= __float_as_int(s1.y));
         if (win) {
-          const float w = blend_weight(s0.w, q);
-          float gd = -s1.y;
+          const float w = blend_weight(s0.z, q);
+          float gd = -s0.w;
 #pragma unroll
           for (int c = 0; c < NCR; ++c)
             if (NC > 0 || c < n) gd = fmaf(s_gh[c * NT + i], cc[c], gd);
@@ -700,35 +835,121 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
     __syncthreads();
     if ((int)threadIdx.x < C && (unsigned)gid < (unsigned)p.N) {
       float T[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      float Tc[NCR];
+#pragma unroll
+      for (int c = 0; c < NCR; ++c) Tc[c] = 0.0f;
       for (int g2 = 0; g2 < G; ++g2) {
         const float* src = s_part + (g2 * C + j) * np;
 #pragma unroll
         for (int k = 0; k < 5; ++k) T[k] += src[k];
+#pragma unroll
+        for (int c = 0; c < NCR; ++c)
+          if (NC > 0 || c < n) Tc[c] += src[5 + c];
       }
-      const GRec rc = p.rec[gid];
-      const float2 cs = p.trig[gid];
-      const float A00 = rc.a.z, B = rc.a.w, A11 = rc.b.x, t1 = rc.b.z, t2 = rc.b.w;
-      const float T1 = t1 * t1, T2 = t2 * t2;
-      const float c2 = cs.x * cs.x, s2 = cs.y * cs.y, sc = cs.x * cs.y;
-      // q = A00 dx^2 + B dx dy + A11 dy^2, d = x - mu_px
-      const float d_mx = -(2.0f * A00 * T[0] + B * T[1]);
-      const float d_my = -(B * T[0] + 2.0f * A11 * T[1]);
-      const float dT1 = T[2] * c2 + T[4] * s2 + 2.0f * T[3] * sc;
-      const float dT2 = T[2] * s2 + T[4] * c2 - 2.0f * T[3] * sc;
-      const float d_th = (T1 - T2) * (2.0f * sc * (T[4] - T[2]) + 2.0f * (c2 - s2) * T[3]);
-      float* gdst = p.grad + (int64_t)gid * np;
-      atomicAdd(gdst + 0, d_mx * (float)t.W);
-      atomicAdd(gdst + 1, d_my * (float)t.H);
-      atomicAdd(gdst + 2, d_th);
-      atomicAdd(gdst + 3, 2.0f * t1 * dT1);
-      atomicAdd(gdst + 4, 2.0f * t2 * dT2);
-      for (int c = 0; c < n; ++c) {
-        float sc_ = 0.0f;
-        for (int g2 = 0; g2 < G; ++g2) sc_ += s_part[(g2 * C + j) * np + 5 + c];
-        atomicAdd(gdst + 5 + c, -2.0f * sc_);  // w g / Z = w * (-2 gh)
-      }
+      emit_grad<NC>(p, t, gid, T, Tc);
     }
     __syncthreads();
+  }
+}
+
+// Adjoint of one tile: passes A and B per pixel, then pass C per candidate.
+template <int TILE, int K, int NC, int CH>
+__device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t, float* smem) {
+  constexpr int NT = TILE * TILE;
+  constexpr int NCR = Chan<NC>::R;
+  const int n = nchan<NC>(p);
+  const BwdSmem SL = bwd_smem(NT, n, CH);
+  float4* s_a = reinterpret_cast<float4*>(smem + SL.a);
+  float2* s_b = reinterpret_cast<float2*>(smem + SL.b);
+  float* s_col = smem + SL.col;
+  float4* s_ps0 = reinterpret_cast<float4*>(smem + SL.ps0);
+  float* s_gh = smem + SL.gh;
+  float* s_slot_a = smem + SL.slot_a;
+  float* s_slot_b = smem + SL.slot_b;
+  float2* s_e = reinterpret_cast<float2*>(s_slot_a);      // until pass C
+  unsigned* s_key = reinterpret_cast<unsigned*>(s_slot_b);  // while staging
+  unsigned* s_mask = reinterpret_cast<unsigned*>(smem + SL.mask);
+  float2* s_ps1 = reinterpret_cast<float2*>(smem + SL.mask);  // chunked path only
+  double* s_loss = reinterpret_cast<double*>(smem + SL.loss);
+
+  const int2 lp = pixel_of<TILE>(threadIdx.x);
+  const int x = t.x0 + lp.x, y = t.y0 + lp.y;
+  const float px = (float)x + 0.5f, py = (float)y + 0.5f;
+  const bool in_img = x < t.W && y < t.H;
+  const int64_t plane = (int64_t)t.H * t.W;
+  const int64_t o = t.off + (int64_t)y * t.W + x;
+  // the pixel's target (or upstream gradient) is read now so that its HBM
+  // latency hides behind passes A and B (fixed channel counts only)
+  const float* src = p.grad_img ? p.grad_img : p.target;
+  constexpr int NUP = NC > 0 ? NC : 1;
+  float up[NUP];
+#pragma unroll
+  for (int c = 0; c < NUP; ++c) up[c] = (NC > 0 && in_img) ? src[c * plane + o] : 0.0f;
+
+  // ---- passes A and B: per-pixel forward values and upstream gradient
+  const int len = t.range.y - t.range.x;
+  const bool fast = len <= CH;
+  float tq[KS<K>::A];
+  PixelBlend<NCR> r;
+  __syncthreads();  // the previous tile of a persistent CTA is done with smem
+  if (fast) {
+    stage_sorted<CH, NC>(p, t.range.x, len, (float)t.x0 + 0.5f * TILE,
+                         (float)t.y0 + 0.5f * TILE, s_a, s_b, s_e, s_col, s_key);
+    __syncthreads();
+    const float4 R = block_rect<TILE>(t.x0, t.y0);
+    float mdrop;
+    culled_keys<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tq, mdrop);
+    culled_blend<K, NC, CH, true>(p, len, px, py, in_img, R, tq, mdrop, s_a, s_b, s_e, s_col,
+                                  s_mask + (threadIdx.x >> 5) * CH, r);
+  } else {
+    select_keys<TILE, K, CH>(p, t.range, px, py, tq, s_a, s_b);
+    blend_pass<TILE, K, NC, CH>(p, t.range, px, py, tq, r, s_a, s_b, s_col);
+  }
+
+  float loss = 0.0f;
+  const bool live = in_img && r.Z > 0.0f;
+  float beta = 0.0f;
+  const float iz = live ? (p.normalize ? 1.0f / r.Z : 1.0f) : 0.0f;
+#pragma unroll
+  for (int c = 0; c < NCR; ++c) {
+    if (NC > 0 || c < n) {
+      float g = 0.0f;
+      if (live) {
+        const float u = NC > 0 ? up[NC > 0 ? c : 0] : src[c * plane + o];
+        if (p.grad_img) {
+          g = u;
+        } else {
+          const float d = r.cr[c] - u;
+          loss += fabsf(d);
+          g = sign_f(d) * t.inv_count;
+        }
+      }
+      const float gh = -0.5f * g * iz;  // dL/dq_k = w_k * (sum_c gh_c c_k,c - beta)
+      if (p.normalize) beta = fmaf(gh, r.cr[c], beta);
+      s_gh[c * NT + threadIdx.x] = gh;
+    }
+  }
+  s_ps0[threadIdx.x] = make_float4(px, py, r.q0, beta);
+  if (!fast) s_ps1[threadIdx.x] = make_float2(live ? r.tau : -F_INF, __int_as_float(r.gcut));
+  if (!p.grad_img) {
+    const double l = warp_sum<double>((double)loss);
+    if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = l;
+  }
+  __syncthreads();
+  if (!p.grad_img && threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int i = 0; i < NT / 32; ++i) tot += s_loss[i];
+    if (tot != 0.0) atomicAdd(t.loss_acc, tot);
+  }
+
+  // ---- pass C: candidate-major accumulation of the adjoint
+  if (fast) {
+    flat_pass_c<TILE, NC, CH>(p, t, len, s_a, s_b, s_col, s_mask, s_ps0, s_gh, s_slot_a,
+                              s_slot_b, reinterpret_cast<int*>(smem + SL.coff),
+                              reinterpret_cast<int*>(smem + SL.scan),
+                              reinterpret_cast<short*>(smem + SL.start));
+  } else {
+    chunked_pass_c<TILE, NC, CH>(p, t, s_ps0, s_ps1, s_gh, s_slot_a);
   }
 }
 
@@ -745,7 +966,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(RenderParams p) {
   t.off = 0;
   t.inv_count = p.inv_count;
   t.loss_acc = &p.status->loss_sum;
-  bwd_tile<TILE, K, NC, TILE * TILE / 2>(p, t, smem);  // 128 Gaussians per stage at 16x16
+  bwd_tile<TILE, K, NC, TILE * TILE>(p, t, smem);  // the whole tile's pixels per stage
 }
 
 __device__ __forceinline__ int image_of_tile(const BatchTables& bt, int tile) {

@@ -13,7 +13,7 @@ cudaError_t fwd_inst(const RenderParams& p, unsigned grid, cudaStream_t s) {
 
 template <int KK, int NCC>
 cudaError_t bwd_inst(const RenderParams& p, unsigned grid, cudaStream_t s) {
-  const size_t bytes = sizeof(float) * (size_t)bwd_smem(16 * 16, NCC > 0 ? NCC : p.n, 16 * 16 / 2).total;
+  const size_t bytes = sizeof(float) * (size_t)bwd_smem(16 * 16, NCC > 0 ? NCC : p.n, 16 * 16).total;
   if (bytes > 48 * 1024) {
     static bool raised = false;  // idempotent; a repeated call is harmless
     if (!raised) {
@@ -63,7 +63,7 @@ template <int KK, int NCC, int CH>
 cudaError_t bwd_batch_inst(const RenderParams& p, const BatchTables& bt, int grid,
                            cudaStream_t s) {
   const size_t bytes = sizeof(float) * (size_t)bwd_smem(16 * 16, NCC > 0 ? NCC : p.n, CH).total;
-  if (bytes > 40 * 1024) {
+  if (bytes > 48 * 1024) {
     static bool raised = false;  // idempotent; a repeated call is harmless
     if (!raised) {
       cudaError_t e = cudaFuncSetAttribute(k_render_bwd_batch<16, KK, NCC, CH>,

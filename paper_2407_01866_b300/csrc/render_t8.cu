@@ -13,7 +13,7 @@ cudaError_t fwd_inst(const RenderParams& p, unsigned grid, cudaStream_t s) {
 
 template <int KK, int NCC>
 cudaError_t bwd_inst(const RenderParams& p, unsigned grid, cudaStream_t s) {
-  const size_t bytes = sizeof(float) * (size_t)bwd_smem(8 * 8, NCC > 0 ? NCC : p.n, 8 * 8 / 2).total;
+  const size_t bytes = sizeof(float) * (size_t)bwd_smem(8 * 8, NCC > 0 ? NCC : p.n, 8 * 8).total;
   if (bytes > 48 * 1024) {
     static bool raised = false;  // idempotent; a repeated call is harmless
     if (!raised) {
