@@ -212,3 +212,59 @@ def test_ablation_modes_forward_adjoint_decode(case):
     pts = synth.query_points(500, H, W, seed=seed)
     dec = O.render_points(g, pts.astype(np.float64), H, W, K=Ko, tile=tile, normalize=bool(norm))
     assert np.abs(gs.decode(pts) - dec).max() <= PIX_TOL * scale
+
+
+def dup_set(M, copies, n, seed, s_range=(0.5, 8.0)):
+    """M Gaussians, each present `copies` times at scattered indices: equal
+    parameters give bit-equal keys, so top-K boundaries fall inside groups of
+    equal keys and the index order must decide (Sec. 3.2 ranking, ties to the
+    smaller index)."""
+    d = synth.gaussians(M, n, seed, s_range=s_range)
+    idx = np.random.default_rng(seed + 50).permutation(np.repeat(np.arange(M), copies))
+    return O.Gaussians(d["xy"][idx], d["theta"][idx], d["inv_scale"][idx], d["color"][idx])
+
+
+def boundary_ties(g, H, W, K, tile):
+    """Pixels whose K-th and (K+1)-th smallest keys are equal."""
+    mx, my = O.means_px32(g, H, W)
+    A00, B, A11 = O.conic32(g)
+    count = 0
+    for ty in range(-(-H // tile)):
+        for tx in range(-(-W // tile)):
+            mem = np.nonzero(O.tile_members(g, tx, ty, tile, H, W))[0]
+            if len(mem) <= K:
+                continue
+            hh, ww = np.meshgrid(np.arange(ty * tile, min(H, ty * tile + tile)),
+                                 np.arange(tx * tile, min(W, tx * tile + tile)), indexing="ij")
+            px = (ww.ravel() + 0.5).astype(np.float32)[:, None]
+            py = (hh.ravel() + 0.5).astype(np.float32)[:, None]
+            q = np.sort(O.rank_key32(px, py, mx[mem][None], my[mem][None], A00[mem][None],
+                                     B[mem][None], A11[mem][None]), axis=1)
+            count += int((q[:, K - 1] == q[:, K]).sum())
+    return count
+
+
+TIES = [
+    # (H, W, M, copies, n, K, tile, seed, s_range)
+    (48, 40, 60, 3, 3, 4, 16, 11, (0.5, 8.0)),     # one-stage lists
+    (32, 32, 40, 4, 1, 10, 8, 12, (0.5, 8.0)),     # 8x8 tiles
+    (16, 16, 100, 3, 3, 10, 16, 13, (2.0, 20.0)),  # one tile of 300: chunked passes
+]
+
+
+@pytest.mark.parametrize("case", TIES, ids=lambda c: f"{c[0]}x{c[1]}_M{c[2]}x{c[3]}_K{c[5]}_t{c[6]}")
+def test_equal_keys_at_the_kth_place_go_to_smaller_indices(case):
+    H, W, M, copies, n, K, tile, seed, sr = case
+    g = dup_set(M, copies, n, seed, sr)
+    assert boundary_ties(g, H, W, K, tile) > 0
+    gs = GpuSet(g, H, W, K, tile)
+    assert np.abs(gs.forward() - O.render_image(g, H, W, K=K, tile=tile)).max() <= PIX_TOL
+    gimg = np.random.default_rng(seed + 100).standard_normal((n, H, W)).astype(np.float32)
+    got, _ = gs.backward(grad_img=gimg)
+    want = O.backward_image(g, gimg, H, W, K=K, tile=tile)
+    errs = grad_rel_error(got, want)
+    assert max(errs.values()) <= GRAD_TOL, errs
+    pix = np.stack(np.meshgrid(np.arange(H), np.arange(W), indexing="ij"), -1).reshape(-1, 2)
+    cen = O.pixel_centres(pix)
+    dec = gs.decode(cen.astype(np.float32))
+    assert np.abs(dec - O.render_points(g, cen, H, W, K=K, tile=tile)).max() <= PIX_TOL
