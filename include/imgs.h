@@ -123,7 +123,9 @@ typedef struct {
   int64_t N, m_capacity;
   const int32_t* tile_range;  /* [T][2] = [start, end) into list */
   const int32_t* list;        /* [m_capacity] Gaussian indices grouped by
-                                 tile, ascending within a tile */
+                                 tile; ascending within a tile of more than
+                                 tile*tile entries, in no set order within
+                                 a shorter one (the renderer ranks those) */
   const float* rec;           /* [N][8] preprocessed geometry (internal) */
   const float* trig;          /* [N][2] (cos, sin) (internal) */
   const float* color;         /* [N][n] float32 colours (internal) */
@@ -151,7 +153,8 @@ int igs_workspace_size(int64_t N, int32_t n, int32_t H, int32_t W,
 
 /* "Project/bin Gaussians to tiles" (Sec. 3.2): per-Gaussian preprocessing
  * (Eq. 2 inverse covariance, 3-sigma circle), exact tile-circle tests,
- * per-tile lists by stable key sort and prefix sums. `ws` is a device buffer
+ * per-tile lists by prefix sums and slot cursors, lists longer than one
+ * tile's pixel count sorted by index. `ws` is a device buffer
  * of at least igs_workspace_size() bytes, 256-byte aligned. Resets the status
  * block. If M > m_capacity the lists are truncated and IGS_FLAG_CAPACITY is
  * raised on the device (no host sync here: read it with igs_read_stats;

@@ -237,7 +237,9 @@ int igs_preprocess_bin(const igs_gaussians* g, int32_t H, int32_t W, const igs_c
   p.status = status;
   unsigned long long* part = reinterpret_cast<unsigned long long*>(base + L.part);
   int2* range = reinterpret_cast<int2*>(base + L.range);
-  IGS_CUDA(run_binning(p, g->dtype, L.tiles_x * L.tiles_y, part, range, s), "binning");
+  // lists up to one render stage (tile^2 entries) are ranked by the renderer
+  IGS_CUDA(run_binning(p, g->dtype, L.tiles_x * L.tiles_y, part, range, cfg->tile * cfg->tile, s),
+           "binning");
   const unsigned int* vals = p.vals;
 
   out->H = H;

@@ -22,6 +22,7 @@ namespace igs {
 namespace {
 
 constexpr int BATCH_TILE = 16;
+constexpr int BATCH_MIN_STAGE = 64;  // smallest one-stage list of the batched adjoint
 
 struct BatchGeom {
   WsLayout L;
@@ -143,7 +144,7 @@ int batch_bin(const igs_fit_state* st, const BatchGeom& G, const igs_config* cfg
   p.tile_off = reinterpret_cast<const int*>(base + G.tile_off);
   unsigned long long* part = reinterpret_cast<unsigned long long*>(base + L.part);
   int2* range = reinterpret_cast<int2*>(base + L.range);
-  BCUDA(run_binning(p, IGS_F32, (int)G.T, part, range, s), "batch: binning");
+  BCUDA(run_binning(p, IGS_F32, (int)G.T, part, range, BATCH_MIN_STAGE, s), "batch: binning");
   BCUDA(launch_tile_evals_batch(range, (int)G.T, p.img_dims, p.tile_off, G.B, BATCH_TILE,
                                 status, s),
         "batch: evals");

@@ -8,9 +8,12 @@
 //   scan           exclusive prefix sum of the tile counters -> list offsets, M
 //   k_emit         every hit takes a slot of its tile's segment (atomic cursor)
 //   k_segsort      one warp per tile sorts its segment by Gaussian index
-//                  (ascending index is the tie-break order of the top-K
-//                  ranking); segments longer than one warp's shared-memory
-//                  window are sorted by whole CTAs in k_segsort_big
+//                  when it is longer than the renderer's one-stage list
+//                  (longer lists are streamed in index order, which is the
+//                  tie-break order of the top-K ranking; shorter ones are
+//                  ranked by the renderer itself); segments longer than one
+//                  warp's shared-memory window are sorted by whole CTAs in
+//                  k_segsort_big
 //   k_ranges       [start, end) of every tile from the offsets, and the sum
 //                  over tiles of |S_j| * pixels(j)
 #include <algorithm>
@@ -292,10 +295,12 @@ __device__ __forceinline__ void tile_segment(const unsigned long long* toff, int
 constexpr int SEG_WARP_MAX = 1024;  // longest segment one warp sorts in shared memory
 constexpr int SEG_BIG_CHUNK = 4096; // run length a CTA sorts in shared memory
 
-// One warp per tile: ascending sort of the tile's Gaussian indices.
+// One warp per tile: ascending sort of the tile's Gaussian indices, for
+// segments longer than sort_min.
 __global__ void __launch_bounds__(256) k_segsort(unsigned int* vals,
                                                  const unsigned long long* toff, int T,
-                                                 DevStatus* st, int64_t m_cap, int* big) {
+                                                 DevStatus* st, int64_t m_cap, int* big,
+                                                 int sort_min) {
   __shared__ unsigned int sh[8][SEG_WARP_MAX];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = blockIdx.x * 8 + warp;
@@ -303,7 +308,7 @@ __global__ void __launch_bounds__(256) k_segsort(unsigned int* vals,
   int64_t a, b;
   tile_segment(toff, t, T, st, m_cap, a, b);
   const int L = (int)(b - a);
-  if (L <= 1) return;
+  if (L <= 1 || L <= sort_min) return;
   if (L > SEG_WARP_MAX) {
     if (lane == 0) big[atomicAdd(&st->big_cnt, 1u)] = t;
     return;
@@ -527,7 +532,7 @@ cudaError_t launch_scan_u32_to_u64(const unsigned int* in, unsigned long long* o
 }
 
 cudaError_t run_binning(const PrepParams& p, int dtype, int T, unsigned long long* part,
-                        int2* range, cudaStream_t s) {
+                        int2* range, int sort_min, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(p.tcnt, 0, sizeof(unsigned int) * (size_t)T, s);
   if (e != cudaSuccess) return e;
   if ((e = launch_preprocess(p, dtype, s)) != cudaSuccess) return e;
@@ -540,7 +545,7 @@ cudaError_t run_binning(const PrepParams& p, int dtype, int T, unsigned long lon
   if ((e = launch_emit(p, s)) != cudaSuccess) return e;
   if (batch) k_wide<true, false><<<148 * 4, 256, 0, s>>>(p);
   else k_wide<false, false><<<148 * 4, 256, 0, s>>>(p);
-  if ((e = launch_segsort(p.vals, p.tmp, p.toff, T, p.status, p.m_cap, p.big, s)) !=
+  if ((e = launch_segsort(p.vals, p.tmp, p.toff, T, p.status, p.m_cap, p.big, sort_min, s)) !=
       cudaSuccess)
     return e;
   return launch_ranges(p.toff, range, T, p.m_cap, p.H, p.W, p.tile,
@@ -549,9 +554,10 @@ cudaError_t run_binning(const PrepParams& p, int dtype, int T, unsigned long lon
 
 cudaError_t launch_segsort(unsigned int* vals, unsigned int* tmp,
                            const unsigned long long* toff, int T, DevStatus* status,
-                           int64_t m_cap, int* big, cudaStream_t s) {
+                           int64_t m_cap, int* big, int sort_min, cudaStream_t s) {
   if (T == 0) return cudaSuccess;
-  k_segsort<<<(unsigned)((T + 7) / 8), 256, 0, s>>>(vals, toff, T, status, m_cap, big);
+  k_segsort<<<(unsigned)((T + 7) / 8), 256, 0, s>>>(vals, toff, T, status, m_cap, big,
+                                                    sort_min);
   k_segsort_big<<<148, 1024, 0, s>>>(vals, tmp, toff, T, status, m_cap, big);
   return cudaGetLastError();
 }

@@ -75,18 +75,17 @@ __device__ __forceinline__ float rank_key(float px, float py, float mx, float my
   return __fmaf_rn(h, dx, __fmul_rn(__fmul_rn(A11, dy), dy));
 }
 
-// Sorted insertion of (q, id) into ascending tq[0..K-1] / tid[0..K-1],
-// dropping the largest: the candidate bubbles down the list, swapping with
-// every entry whose key is larger. Equal keys keep the earlier entry first, so
-// feeding candidates in ascending index order breaks ties toward the smaller
-// index.
+// Sorted insertion of (q, id) into tq[0..K-1] / tid[0..K-1], ascending in
+// the (key, index) order, dropping the largest: the candidate bubbles down
+// the list, swapping with every entry that follows it in that order. The
+// result does not depend on the order candidates arrive in.
 template <int K>
 __device__ __forceinline__ void topk_insert(float (&tq)[K], int (&tid)[K], float q, int id) {
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const float oq = tq[k];
     const int oi = tid[k];
-    const bool sw = q < oq;
+    const bool sw = q < oq || (q == oq && id < oi);
     tq[k] = sw ? q : oq;
     tid[k] = sw ? id : oi;
     q = sw ? oq : q;

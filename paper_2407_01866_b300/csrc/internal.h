@@ -99,16 +99,19 @@ cudaError_t launch_tile_evals_batch(const int2* range, int T, const int4* dims,
 cudaError_t launch_scan_u32_to_u64(const unsigned int* in, unsigned long long* out, int64_t n,
                                    unsigned long long* part, unsigned long long* total,
                                    cudaStream_t s);
+// Sorts every tile segment longer than sort_min by Gaussian index.
 cudaError_t launch_segsort(unsigned int* vals, unsigned int* tmp,
                            const unsigned long long* toff, int T, DevStatus* status,
-                           int64_t m_cap, int* big, cudaStream_t s);
+                           int64_t m_cap, int* big, int sort_min, cudaStream_t s);
 cudaError_t launch_ranges(const unsigned long long* toff, int2* range, int T, int64_t m_cap,
                           int H, int W, int tile, int tiles_x, DevStatus* status,
                           cudaStream_t s);
 // Whole binning sequence after the status reset: per-tile counts, scan,
 // emit, segment sort, ranges (and, for one image, the evaluation count).
+// Segments of at most sort_min entries (the renderer's one-stage capacity)
+// are left in emission order; longer ones are sorted by Gaussian index.
 cudaError_t run_binning(const PrepParams& p, int dtype, int T, unsigned long long* part,
-                        int2* range, cudaStream_t s);
+                        int2* range, int sort_min, cudaStream_t s);
 
 // Render family: return cudaErrorInvalidValue for an unsupported (tile, K, n).
 cudaError_t launch_render_fwd(const RenderParams& p, int tile, int K, cudaStream_t s);

@@ -138,9 +138,9 @@ __device__ __forceinline__ void stage_chunk(const RenderParams& p, int base, int
 }
 
 // Fast path: stage the whole list (cnt <= NT <= blockDim.x), each record at
-// its rank in the order of the candidates' keys at (cx, cy) (ties, and the
-// low 8 bits of each key, broken by list position). s_key holds NT words
-// (16-byte aligned) of scratch that must not overlap the staged arrays.
+// its rank in the (key at (cx, cy), index) order, which does not depend on
+// the order of the list. s_key holds 2 NT words (16-byte aligned) of scratch
+// that must not overlap the staged arrays.
 template <int NT, int NC>
 __device__ __forceinline__ void stage_sorted(const RenderParams& p, int base, int cnt, float cx,
                                              float cy, float4* s_a, float2* s_b, float2* s_e,
@@ -150,32 +150,32 @@ __device__ __forceinline__ void stage_sorted(const RenderParams& p, int base, in
   GRec g;
   float col[NCS];
   int gid = -1;
-  unsigned key = 0xffffffffu;  // padding: never below a real key
+  unsigned key = 0xffffffffu, kid = 0xffffffffu;  // padding: after every real entry
   if (j < cnt) {
     const int e = p.list[base + j];
+    kid = 0x80000000u | (unsigned)j;  // a corrupt entry: unique, after every index
     if ((unsigned)e < (unsigned)p.N) {
+      kid = (unsigned)e;
       gid = e;
       g = p.rec[gid];
       if (NC > 0) {
 #pragma unroll
         for (int c = 0; c < NCS; ++c) col[c] = p.color[(int64_t)gid * NC + c];
       }
-      const float kc = fmaxf(rank_key(cx, cy, g.a.x, g.a.y, g.a.z, g.a.w, g.b.x), 0.0f);
-      key = (__float_as_uint(kc) & 0xffffff00u) | (unsigned)j;
-    } else {
-      key = 0xffffff00u | (unsigned)j;
+      key = __float_as_uint(fmaxf(rank_key(cx, cy, g.a.x, g.a.y, g.a.z, g.a.w, g.b.x), 0.0f));
     }
   }
-  const int cnt4 = (cnt + 3) & ~3;
-  if (j < cnt4) s_key[j] = key;
+  // 64-bit (key, index) words: one unsigned compare orders them
+  const unsigned long long mine = ((unsigned long long)key << 32) | kid;
+  const int cnt2 = (cnt + 1) & ~1;
+  if (j < cnt2) reinterpret_cast<unsigned long long*>(s_key)[j] = mine;
   __syncthreads();
   if (j < cnt) {
     int r = 0;
-    const uint4* k4 = reinterpret_cast<const uint4*>(s_key);
-    for (int i = 0; i < cnt4 / 4; ++i) {
-      const uint4 v = k4[i];
-      r += (v.x < key ? 1 : 0) + (v.y < key ? 1 : 0) + (v.z < key ? 1 : 0) +
-           (v.w < key ? 1 : 0);
+    const ulonglong2* k2 = reinterpret_cast<const ulonglong2*>(s_key);
+    for (int i = 0; i < cnt2 / 2; ++i) {
+      const ulonglong2 v = k2[i];
+      r += (v.x < mine ? 1 : 0) + (v.y < mine ? 1 : 0);
     }
     if (gid >= 0) {
       const float d = g.b.z * g.b.w;
@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(RenderParams p) {
   __shared__ float4 s_a[NT];
   __shared__ float2 s_b[NT];
   __shared__ float2 s_e[NT];
-  __shared__ __align__(16) unsigned s_key[NT];
+  __shared__ __align__(16) unsigned s_key[2 * NT];
   __shared__ float s_col[NT * (NC > 0 ? NC : 1)];
   const int tile_id = blockIdx.x;
   const int x0 = (tile_id % p.tiles_x) * TILE, y0 = (tile_id / p.tiles_x) * TILE;
@@ -1062,7 +1062,8 @@ __global__ void __launch_bounds__(256) k_decode(RenderParams p) {
       if ((unsigned)id >= (unsigned)p.N) continue;
       const GRec g = p.rec[id];
       const float q = rank_key(px, py, g.a.x, g.a.y, g.a.z, g.a.w, g.b.x);
-      if (q < tq[KS<K>::A - 1]) topk_insert<KS<K>::A>(tq, tp, q, id);
+      if (q < tq[KS<K>::A - 1] || (q == tq[KS<K>::A - 1] && id < tp[KS<K>::A - 1]))
+        topk_insert<KS<K>::A>(tq, tp, q, id);
     }
     const float q0 = p.normalize ? tq[0] : 0.0f;
 #pragma unroll

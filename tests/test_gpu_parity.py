@@ -53,7 +53,9 @@ def test_tile_lists_equal_oracle_sets(case):
     got = gs.tile_lists()
     assert len(got) == len(want)
     for j, (a, b) in enumerate(zip(got, want)):
-        np.testing.assert_array_equal(a, b, err_msg=f"tile {j}")
+        # lists up to tile*tile entries come in no set order; longer ones ascending
+        np.testing.assert_array_equal(a if len(a) > tile * tile else np.sort(a), b,
+                                      err_msg=f"tile {j}")
     assert gs.stats.m_needed == sum(len(w) for w in want)
     assert gs.stats.evals == O.count_evals(g, H, W, tile)
     assert gs.stats.flags == 0
