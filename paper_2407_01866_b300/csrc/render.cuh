@@ -79,23 +79,36 @@ constexpr int GID_NONE = 0x7fffffff;  // tie cut-off that admits every index
 // Staged candidate record in shared memory:
 //   a = (mx, my, A00, B)   geometry of the ranking key
 //   b = (A11, index as int bits)
-//   e = (ex, ey) = (det/A11, det/A00) with det = A00 A11 - B^2/4 = (t1 t2)^2,
-//       so that q >= ex dx^2 and q >= ey dy^2 for every displacement
-//       (fast path only).
+//   e = (1/(2 A00), 1/(2 A11)), the minimiser of q along one axis for a
+//       fixed displacement along the other (fast path only).
 
 // Lower bound of the ranking key of staged record (a, a11, e) at every pixel
-// centre of rectangle R, valid for the float32 evaluation of rank_key: the
-// axis-wise bounds over the rectangle, reduced by a relative 1e-5 and by
-// 2e-6 times the largest sum of term magnitudes |A00| dx^2 + |B dx dy| +
-// A11 dy^2 over R (float32 rounding of the key, of the staged conic and of
-// this bound are each a few 2^-24 of those).
+// centre of the rectangle R = [x_lo, x_hi] x [y_lo, y_hi], valid for the
+// float32 evaluation of rank_key. q is a convex quadratic of the
+// displacement d = p - mu; unless mu lies in R, its minimum over R lies on a
+// face of R that faces mu, and on such a face (dx fixed) the minimum is at
+// dy = -B dx / (2 A11) clamped to the face. The smaller of the (at most two)
+// facing faces' minima is reduced by a relative 1e-5 and by 2e-6 times the
+// largest sum of term magnitudes |A00| dx^2 + |B dx dy| + A11 dy^2 over R
+// (float32 rounding of the key, of the staged conic and of this bound are
+// each a few 2^-24 of those).
 __device__ __forceinline__ float key_lower_bound(const float4& a, float a11, const float2& e,
                                                  const float4& R) {
-  const float ddx = fmaxf(fmaxf(R.x - a.x, a.x - R.y), 0.0f);
-  const float ddy = fmaxf(fmaxf(R.z - a.y, a.y - R.w), 0.0f);
-  const float L = fmaxf(ddx * ddx * e.x, ddy * ddy * e.y);
-  const float fx = fmaxf(fabsf(R.x - a.x), fabsf(R.y - a.x));
-  const float fy = fmaxf(fabsf(R.z - a.y), fabsf(R.w - a.y));
+  const float ux0 = R.x - a.x, ux1 = R.y - a.x;  // range of dx over R
+  const float uy0 = R.z - a.y, uy1 = R.w - a.y;  // range of dy over R
+  // face facing mu in x (dx fixed to the near edge), dy minimising, clamped
+  const float fdx = ux0 > 0.0f ? ux0 : ux1;
+  const float fdy = fminf(fmaxf(-a.w * fdx * e.y, uy0), uy1);
+  const float qx = fmaf(fmaf(a.z, fdx, a.w * fdy), fdx, a11 * fdy * fdy);
+  // face facing mu in y
+  const float gdy = uy0 > 0.0f ? uy0 : uy1;
+  const float gdx = fminf(fmaxf(-a.w * gdy * e.x, ux0), ux1);
+  const float qy = fmaf(fmaf(a11, gdy, a.w * gdx), gdy, a.z * gdx * gdx);
+  const bool xin = ux0 <= 0.0f && ux1 >= 0.0f;
+  const bool yin = uy0 <= 0.0f && uy1 >= 0.0f;
+  const float L = (xin && yin) ? 0.0f : fminf(xin ? F_INF : qx, yin ? F_INF : qy);
+  const float fx = fmaxf(fabsf(ux0), fabsf(ux1));
+  const float fy = fmaxf(fabsf(uy0), fabsf(uy1));
   const float hb = 0.5f * fabsf(a.w);
   const float M = (fabsf(a.z) + hb) * fx * fx + (a11 + hb) * fy * fy;
   return fmaf(L, 1.0f - 1e-5f, -2e-6f * M);
@@ -178,11 +191,9 @@ __device__ __forceinline__ void stage_sorted(const RenderParams& p, int base, in
       r += (v.x < mine ? 1 : 0) + (v.y < mine ? 1 : 0);
     }
     if (gid >= 0) {
-      const float d = g.b.z * g.b.w;
-      const float det = d * d;
       s_a[r] = g.a;
       s_b[r] = make_float2(g.b.x, __int_as_float(gid));
-      s_e[r] = make_float2(det / g.b.x, det / g.a.z);
+      s_e[r] = make_float2(0.5f / g.a.z, 0.5f / g.b.x);
       if (NC > 0) {
 #pragma unroll
         for (int c = 0; c < NCS; ++c) s_col[c * NT + r] = col[c];
