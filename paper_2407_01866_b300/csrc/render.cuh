@@ -509,7 +509,7 @@ struct TileCtx {
 // Dynamic shared-memory layout of the adjoint kernel (in 4-byte words), for
 // NT pixels, n channels and CH Gaussians per stage (64 <= CH <= NT).
 struct BwdSmem {
-  int a, b, col, ps0, gh, slot_a, slot_b, mask, coff, start, loss, scan, total;
+  int a, b, col, ps0, gh, slot_a, slot_b, mask, coff, loss, scan, total;
 };
 __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   const int NWB = NT / 32;
@@ -524,9 +524,9 @@ __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   L.gh = o;     o = al4(o + n * NT);      // per-pixel -g/(2Z), channel-major
   L.slot_a = o; o = al4(o + np * CH);     // pass C per-candidate sums; (ex, ey) before
   L.slot_b = o; o = al4(o + np * NT);     // pass C per-thread sums; rank keys before
-  L.mask = o;   o += (NWB * CH > 2 * NT ? NWB * CH : 2 * NT);  // ballots; chunked (tau, cut)
+  // ballots, then pass C's 16-bit pair table (<= 16 NT pairs); chunked (tau, cut-off)
+  L.mask = o;   o += (NWB * CH > 8 * NT ? NWB * CH : 8 * NT);
   L.coff = o;   o += CH + 1;              // first pair of every candidate
-  L.start = o;  o += (NT + 1) / 2;        // shorts: item where each thread's pairs start
   L.loss = (o + 1) & ~1; o = L.loss + 2 * NWB + 2;  // doubles
   L.scan = o;   o += 34;                  // integer block-scan scratch
   L.total = o;
@@ -602,77 +602,70 @@ __device__ __forceinline__ int div_small(int a, int d, float inv) {
   return q;
 }
 
-// Position of the k-th (0-based) set bit of m, for k < popc(m).
-__device__ __forceinline__ int nth_set_bit(unsigned m, int k) {
-  int pos = 0;
-#pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
-    const int c = __popc(m & ((1u << s) - 1u));
-    const bool up = k >= c;
-    k = up ? k - c : k;
-    m = up ? m >> s : m;
-    pos = up ? pos + s : pos;
-  }
-  return pos;
-}
-
 // Pass C of the fast path. The winning (candidate, pixel) pairs, in
-// (candidate, warp block, pixel) order, are split into equal contiguous
-// ranges, one per thread; a thread accumulates the candidates of its range
-// in registers. A candidate's partial sums go to the candidate's slot A_j,
-// written by the one thread whose range holds the candidate's first pair,
-// or, for the candidate a range opens with when it began in an earlier
-// range, to that thread's slot B_t. After a barrier, the thread of candidate
-// j adds A_j and the B_t of the later threads its pairs reach, and turns the
-// sums into parameter gradients.
+// (candidate, warp block, pixel) order, are first written out as a table of
+// 16-bit entries (candidate << 8 | pixel) over the ballot masks' storage (each
+// thread reads its masks into registers before the offset scan's barriers).
+// The table is split into equal contiguous ranges, one per thread; a thread
+// accumulates the candidates of its range in registers. A candidate's partial
+// sums go to the candidate's slot A_j, written by the one thread whose range
+// holds the candidate's first pair, or, for the candidate a range opens with
+// when it began in an earlier range, to that thread's slot B_t. After a
+// barrier, the thread of candidate j adds A_j and the B_t of the later
+// threads its pairs reach, and turns the sums into parameter gradients.
+// Needs at most NT * 16 pairs (K <= 16).
 template <int TILE, int NC, int CH>
 __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx& t, int cnt,
                                             const float4* s_a, const float2* s_b,
-                                            const float* s_col, const unsigned* s_mask,
+                                            const float* s_col, unsigned* s_mask,
                                             const float4* s_ps0, const float* s_gh,
                                             float* s_slot_a, float* s_slot_b, int* s_coff,
-                                            int* s_scan, short* s_start) {
+                                            int* s_scan) {
   constexpr int NT = TILE * TILE;
   constexpr int NWB = NT / 32;
   constexpr int NCR = Chan<NC>::R;
+  constexpr int MAXIT = (NWB * CH + NT - 1) / NT;  // items per thread in the scan
   const int n = nchan<NC>(p);
   const int nit = cnt * NWB;
-  auto mask_of = [&](int it) { return s_mask[(it % NWB) * CH + it / NWB]; };
-  // pair offsets of the items (candidate-major), and where each range starts
+  // item it = (candidate it / NWB, warp block it % NWB); per_it consecutive
+  // items per thread
   const int per_it = (nit + NT - 1) / NT;
   const int i0 = (int)threadIdx.x * per_it;
+  unsigned mk[MAXIT];
   int loc = 0;
-  for (int k = 0; k < per_it; ++k)
-    if (i0 + k < nit) loc += __popc(mask_of(i0 + k));
-  int P;
-  int run = block_scan_int(loc, s_scan, P);
-  const int per = (P + NT - 1) / NT;  // pairs per thread
-  const float inv_per = per > 0 ? 1.0f / (float)per : 0.0f;
-  for (int k = 0; k < per_it; ++k) {
+#pragma unroll
+  for (int k = 0; k < MAXIT; ++k) {
     const int it = i0 + k;
-    if (it < nit) {
-      const int c = __popc(mask_of(it));
-      if (it % NWB == 0) s_coff[it / NWB] = run;
-      if (c > 0) {  // ranges starting at pairs run .. run+c-1
-        const int th0 = div_small(run + per - 1, per, inv_per);
-        const int th1 = div_small(run + c - 1, per, inv_per);
-        for (int th = th0; th <= th1; ++th) s_start[th] = (short)it;
+    mk[k] = (k < per_it && it < nit) ? s_mask[(it % NWB) * CH + it / NWB] : 0u;
+    loc += __popc(mk[k]);
+  }
+  int P;
+  int run = block_scan_int(loc, s_scan, P);  // its barriers end every read of s_mask
+  unsigned short* s_pair = reinterpret_cast<unsigned short*>(s_mask);
+#pragma unroll
+  for (int k = 0; k < MAXIT; ++k) {
+    const int it = i0 + k;
+    if (k < per_it && it < nit) {
+      const int j = it / NWB, wb = it % NWB;
+      if (wb == 0) s_coff[j] = run;
+      unsigned m = mk[k];
+      while (m) {
+        s_pair[run++] = (unsigned short)((j << 8) | (wb * 32 + __ffs(m) - 1));
+        m &= m - 1;
       }
-      run += c;
     }
   }
   if (threadIdx.x == 0) s_coff[cnt] = P;
+  const int per = (P + NT - 1) / NT;  // pairs per thread
+  const float inv_per = per > 0 ? 1.0f / (float)per : 0.0f;
   __syncthreads();
 
   const int r0 = (int)threadIdx.x * per;
   const int r1 = min(P, r0 + per);
   if (r0 < r1) {
-    int it = s_start[threadIdx.x];
-    int j = it / NWB, wb = it - j * NWB;
-    int ioff = s_coff[j];
-    for (int w2 = 0; w2 < wb; ++w2) ioff += __popc(s_mask[w2 * CH + j]);
-    unsigned m = mask_of(it);
-    m &= 0xffffffffu << nth_set_bit(m, r0 - ioff);
+    int e = r0;
+    unsigned ent = s_pair[e];
+    int j = (int)(ent >> 8);
     const int j_first = j;
     const bool cont = s_coff[j] < r0;  // the first candidate began in an earlier range
     float4 a = s_a[j];
@@ -703,9 +696,8 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
         Tc[c] = 0.0f;
       }
     };
-    for (int e = r0; e < r1; ++e) {
-      const int i = wb * 32 + (__ffs(m) - 1);
-      m &= m - 1;
+    for (;;) {
+      const int i = (int)(ent & 255u);
       const float4 s0 = s_ps0[i];  // (px, py, q0, beta)
       // the ranking key of pass A, recomputed bit for bit (same sequence)
       const float dx = __fsub_rn(s0.x, a.x);
@@ -730,20 +722,15 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
 #pragma unroll
       for (int c = 0; c < NCR; ++c)
         if (NC > 0 || c < n) Tc[c] = fmaf(w, gh[c], Tc[c]);
-      if (m == 0 && e + 1 < r1) {
-        do {
-          ++it;
-          m = mask_of(it);
-        } while (m == 0);
-        const int nj = it / NWB;
-        wb = it - nj * NWB;
-        if (nj != j) {
-          flush(j);
-          j = nj;
-          a = s_a[j];
-          a11 = s_b[j].x;
-          load_colour(j);
-        }
+      if (++e >= r1) break;
+      ent = s_pair[e];
+      const int nj = (int)(ent >> 8);
+      if (nj != j) {
+        flush(j);
+        j = nj;
+        a = s_a[j];
+        a11 = s_b[j].x;
+        load_colour(j);
       }
     }
     flush(j);
@@ -910,8 +897,8 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
     const float4 R = block_rect<TILE>(t.x0, t.y0);
     float mdrop;
     culled_keys<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tq, mdrop);
-    culled_blend<K, NC, CH, true>(p, len, px, py, in_img, R, tq, mdrop, s_a, s_b, s_e, s_col,
-                                  s_mask + (threadIdx.x >> 5) * CH, r);
+    culled_blend<K, NC, CH, (K > 0)>(p, len, px, py, in_img, R, tq, mdrop, s_a, s_b, s_e,
+                                     s_col, s_mask + (threadIdx.x >> 5) * CH, r);
   } else {
     select_keys<TILE, K, CH>(p, t.range, px, py, tq, s_a, s_b);
     blend_pass<TILE, K, NC, CH>(p, t.range, px, py, tq, r, s_a, s_b, s_col);
@@ -941,7 +928,10 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
     }
   }
   s_ps0[threadIdx.x] = make_float4(px, py, r.q0, beta);
-  if (!fast) s_ps1[threadIdx.x] = make_float2(live ? r.tau : -F_INF, __int_as_float(r.gcut));
+  // the chunked pass C (long lists; K = 0, where every candidate wins) re-tests
+  // membership from (tau, cut-off)
+  const bool flat = fast && K > 0;
+  if (!flat) s_ps1[threadIdx.x] = make_float2(live ? r.tau : -F_INF, __int_as_float(r.gcut));
   if (!p.grad_img) {
     const double l = warp_sum<double>((double)loss);
     if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = l;
@@ -954,11 +944,10 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   }
 
   // ---- pass C: candidate-major accumulation of the adjoint
-  if (fast) {
+  if (flat) {
     flat_pass_c<TILE, NC, CH>(p, t, len, s_a, s_b, s_col, s_mask, s_ps0, s_gh, s_slot_a,
                               s_slot_b, reinterpret_cast<int*>(smem + SL.coff),
-                              reinterpret_cast<int*>(smem + SL.scan),
-                              reinterpret_cast<short*>(smem + SL.start));
+                              reinterpret_cast<int*>(smem + SL.scan));
   } else {
     chunked_pass_c<TILE, NC, CH>(p, t, s_ps0, s_ps1, s_gh, s_slot_a);
   }
