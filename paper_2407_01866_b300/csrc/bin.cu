@@ -7,8 +7,8 @@
 //                  that tile's counter
 //   scan           exclusive prefix sum of the tile counters -> list offsets, M
 //   k_emit         every hit takes a slot of its tile's segment (atomic cursor)
-//   k_segsort      one warp per tile sorts its segment by Gaussian index
-//                  when it is longer than the renderer's one-stage list
+//   k_segsort      a warp sorts a tile's segment by Gaussian index when it
+//                  is longer than the renderer's one-stage list
 //                  (longer lists are streamed in index order, which is the
 //                  tie-break order of the top-K ranking; shorter ones are
 //                  ranked by the renderer itself); segments longer than one
@@ -295,24 +295,11 @@ __device__ __forceinline__ void tile_segment(const unsigned long long* toff, int
 constexpr int SEG_WARP_MAX = 1024;  // longest segment one warp sorts in shared memory
 constexpr int SEG_BIG_CHUNK = 4096; // run length a CTA sorts in shared memory
 
-// One warp per tile: ascending sort of the tile's Gaussian indices, for
-// segments longer than sort_min.
-__global__ void __launch_bounds__(256) k_segsort(unsigned int* vals,
-                                                 const unsigned long long* toff, int T,
-                                                 DevStatus* st, int64_t m_cap, int* big,
-                                                 int sort_min) {
-  __shared__ unsigned int sh[8][SEG_WARP_MAX];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = blockIdx.x * 8 + warp;
-  if (t >= T) return;
-  int64_t a, b;
-  tile_segment(toff, t, T, st, m_cap, a, b);
-  const int L = (int)(b - a);
-  if (L <= 1 || L <= sort_min) return;
-  if (L > SEG_WARP_MAX) {
-    if (lane == 0) big[atomicAdd(&st->big_cnt, 1u)] = t;
-    return;
-  }
+// Ascending sort of one tile segment [a, a+L) by the calling warp
+// (1 < L <= SEG_WARP_MAX); w is the warp's shared-memory window.
+__device__ __forceinline__ void warp_sort_segment(unsigned int* vals, int64_t a, int L,
+                                                  unsigned int* w) {
+  const int lane = threadIdx.x & 31;
   if (L <= 32) {  // bitonic network across the lanes
     unsigned int v = lane < L ? vals[a + lane] : 0xffffffffu;
 #pragma unroll
@@ -329,7 +316,6 @@ __global__ void __launch_bounds__(256) k_segsort(unsigned int* vals,
   }
   int P = 64;
   while (P < L) P <<= 1;
-  unsigned int* w = sh[warp];
   for (int i = lane; i < P; i += 32) w[i] = i < L ? vals[a + i] : 0xffffffffu;
   __syncwarp();
   for (int k = 2; k <= P; k <<= 1) {
@@ -348,6 +334,36 @@ __global__ void __launch_bounds__(256) k_segsort(unsigned int* vals,
     }
   }
   for (int i = lane; i < L; i += 32) vals[a + i] = w[i];
+  __syncwarp();
+}
+
+// Ascending sort of the tile segments longer than sort_min. Each warp looks
+// at 32 tiles at a time (one coalesced read of their offsets) and sorts the
+// ones that need it; segments longer than one warp's window are listed for
+// k_segsort_big.
+__global__ void __launch_bounds__(256) k_segsort(unsigned int* vals,
+                                                 const unsigned long long* toff, int T,
+                                                 DevStatus* st, int64_t m_cap, int* big,
+                                                 int sort_min) {
+  __shared__ unsigned int sh[8][SEG_WARP_MAX];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * 8;
+  for (int base = (blockIdx.x * 8 + warp) * 32; base < T; base += nwarps * 32) {
+    const int t = base + lane;
+    int64_t a = 0, b = 0;
+    if (t < T) tile_segment(toff, t, T, st, m_cap, a, b);
+    const int L = (int)(b - a);
+    const bool longer = t < T && L > 1 && L > sort_min;
+    if (longer && L > SEG_WARP_MAX) big[atomicAdd(&st->big_cnt, 1u)] = t;
+    unsigned need = __ballot_sync(FULL_MASK, longer && L <= SEG_WARP_MAX);
+    while (need) {
+      const int l = __ffs(need) - 1;
+      need &= need - 1;
+      const long long al = __shfl_sync(FULL_MASK, (long long)a, l);
+      const int Ll = __shfl_sync(FULL_MASK, L, l);
+      warp_sort_segment(vals, al, Ll, sh[warp]);
+    }
+  }
 }
 
 // Long segments, one CTA each: runs of SEG_BIG_CHUNK sorted in shared memory,
@@ -556,8 +572,8 @@ cudaError_t launch_segsort(unsigned int* vals, unsigned int* tmp,
                            const unsigned long long* toff, int T, DevStatus* status,
                            int64_t m_cap, int* big, int sort_min, cudaStream_t s) {
   if (T == 0) return cudaSuccess;
-  k_segsort<<<(unsigned)((T + 7) / 8), 256, 0, s>>>(vals, toff, T, status, m_cap, big,
-                                                    sort_min);
+  const unsigned grid = (unsigned)std::min<int64_t>((T + 255) / 256, 148 * 4);
+  k_segsort<<<grid, 256, 0, s>>>(vals, toff, T, status, m_cap, big, sort_min);
   k_segsort_big<<<148, 1024, 0, s>>>(vals, tmp, toff, T, status, m_cap, big);
   return cudaGetLastError();
 }
