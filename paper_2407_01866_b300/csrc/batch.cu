@@ -112,8 +112,10 @@ BatchTables tables(const BatchGeom& G, char* base, int order) {
 }
 
 // Bins the concatenated Gaussians of the fit state; returns render params.
+// Lists longer than sort_min (the smallest stage the adjoint will run with)
+// are sorted by Gaussian index; shorter ones are ranked by the renderer.
 int batch_bin(const igs_fit_state* st, const BatchGeom& G, const igs_config* cfg, char* base,
-              int64_t m_cap, RenderParams* rp, cudaStream_t s) {
+              int64_t m_cap, int sort_min, RenderParams* rp, cudaStream_t s) {
   const WsLayout& L = G.L;
   DevStatus* status = reinterpret_cast<DevStatus*>(base + L.status);
   BCUDA(cudaMemsetAsync(status, 0, sizeof(DevStatus), s), "batch: reset status");
@@ -144,7 +146,7 @@ int batch_bin(const igs_fit_state* st, const BatchGeom& G, const igs_config* cfg
   p.tile_off = reinterpret_cast<const int*>(base + G.tile_off);
   unsigned long long* part = reinterpret_cast<unsigned long long*>(base + L.part);
   int2* range = reinterpret_cast<int2*>(base + L.range);
-  BCUDA(run_binning(p, IGS_F32, (int)G.T, part, range, BATCH_MIN_STAGE, s), "batch: binning");
+  BCUDA(run_binning(p, IGS_F32, (int)G.T, part, range, sort_min, s), "batch: binning");
   BCUDA(launch_tile_evals_batch(range, (int)G.T, p.img_dims, p.tile_off, G.B, BATCH_TILE,
                                 status, s),
         "batch: evals");
@@ -273,7 +275,7 @@ extern "C" int igs_fit_batch_step(const igs_fit_state* st, const float* d_target
   char* base = static_cast<char*>(ws);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   RenderParams rp;
-  if (int r = batch_bin(st, G, cfg, base, m_capacity, &rp, s)) return r;
+  if (int r = batch_bin(st, G, cfg, base, m_capacity, tn.stage, &rp, s)) return r;
   if (int r = batch_adjoint(st, d_targets, G, cfg, tn, base, rp, s)) return r;
   if (int r = igs_adam_update(st, cfg, stream)) return r;
   BCUDA(launch_finalize_batch(st->step, reinterpret_cast<const double*>(base + G.loss),
@@ -296,7 +298,8 @@ extern "C" int igs_autotune_batch(const igs_fit_state* st, const float* d_target
   char* base = static_cast<char*>(ws);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   RenderParams rp;
-  if (int r = batch_bin(st, G, cfg, base, m_capacity, &rp, s)) return r;
+  // one binning serves every stage tried below
+  if (int r = batch_bin(st, G, cfg, base, m_capacity, BATCH_MIN_STAGE, &rp, s)) return r;
   cudaEvent_t e0, e1;
   BCUDA(cudaEventCreate(&e0), "autotune: event");
   BCUDA(cudaEventCreate(&e1), "autotune: event");

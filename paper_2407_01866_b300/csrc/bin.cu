@@ -292,7 +292,7 @@ __device__ __forceinline__ void tile_segment(const unsigned long long* toff, int
   b = b < M ? b : M;
 }
 
-constexpr int SEG_WARP_MAX = 1024;  // longest segment one warp sorts in shared memory
+constexpr int SEG_WARP_MAX = 64;    // longest segment one warp sorts (latency-bound beyond)
 constexpr int SEG_BIG_CHUNK = 4096; // run length a CTA sorts in shared memory
 
 // Ascending sort of one tile segment [a, a+L) by the calling warp
@@ -339,8 +339,7 @@ __device__ __forceinline__ void warp_sort_segment(unsigned int* vals, int64_t a,
 
 // Ascending sort of the tile segments longer than sort_min. Each warp looks
 // at 32 tiles at a time (one coalesced read of their offsets) and sorts the
-// ones that need it; segments longer than one warp's window are listed for
-// k_segsort_big.
+// short ones that need it; longer segments are listed for k_segsort_big.
 __global__ void __launch_bounds__(256) k_segsort(unsigned int* vals,
                                                  const unsigned long long* toff, int T,
                                                  DevStatus* st, int64_t m_cap, int* big,
@@ -366,11 +365,12 @@ __global__ void __launch_bounds__(256) k_segsort(unsigned int* vals,
   }
 }
 
-// Long segments, one CTA each: runs of SEG_BIG_CHUNK sorted in shared memory,
+// Long segments, one CTA each: runs of up to SEG_BIG_CHUNK sorted in shared
+// memory (bitonic over the run rounded up to a power of two),
 // then pairwise merges between vals and tmp, each element placed by its rank
 // (its index in its own run plus a binary search in the other run; indices
 // are distinct, so the ranks are a permutation).
-__global__ void __launch_bounds__(1024) k_segsort_big(unsigned int* vals, unsigned int* tmp,
+__global__ void __launch_bounds__(256) k_segsort_big(unsigned int* vals, unsigned int* tmp,
                                                       const unsigned long long* toff, int T,
                                                       const DevStatus* st, int64_t m_cap,
                                                       const int* big) {
@@ -383,13 +383,15 @@ __global__ void __launch_bounds__(1024) k_segsort_big(unsigned int* vals, unsign
     const int L = (int)(b - a);
     for (int c0 = 0; c0 < L; c0 += SEG_BIG_CHUNK) {
       const int n = min(SEG_BIG_CHUNK, L - c0);
+      int P = 64;  // bitonic width: the chunk rounded up to a power of two
+      while (P < n) P <<= 1;
       __syncthreads();
-      for (int i = threadIdx.x; i < SEG_BIG_CHUNK; i += blockDim.x)
+      for (int i = threadIdx.x; i < P; i += blockDim.x)
         sh[i] = i < n ? vals[a + c0 + i] : 0xffffffffu;
       __syncthreads();
-      for (int k = 2; k <= SEG_BIG_CHUNK; k <<= 1) {
+      for (int k = 2; k <= P; k <<= 1) {
         for (int j = k >> 1; j > 0; j >>= 1) {
-          for (int i = threadIdx.x; i < SEG_BIG_CHUNK; i += blockDim.x) {
+          for (int i = threadIdx.x; i < P; i += blockDim.x) {
             const int l = i ^ j;
             if (l > i) {
               const unsigned int x = sh[i], y = sh[l];
@@ -574,7 +576,7 @@ cudaError_t launch_segsort(unsigned int* vals, unsigned int* tmp,
   if (T == 0) return cudaSuccess;
   const unsigned grid = (unsigned)std::min<int64_t>((T + 255) / 256, 148 * 4);
   k_segsort<<<grid, 256, 0, s>>>(vals, toff, T, status, m_cap, big, sort_min);
-  k_segsort_big<<<148, 1024, 0, s>>>(vals, tmp, toff, T, status, m_cap, big);
+  k_segsort_big<<<148 * 8, 256, 0, s>>>(vals, tmp, toff, T, status, m_cap, big);
   return cudaGetLastError();
 }
 
