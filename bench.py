@@ -35,6 +35,15 @@ UNIT = "fit steps/s"
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2032.0
+# DRAM bytes (read + write) of one fused forward + L1 + adjoint launch on the
+# fitted 2048^2 RGB state, from the ncu capture summarised in
+# profiles/k_render_fit2048_rgb.md (64.62 MB read + 1.78 MB written); the
+# 2048^2 RGB workload only
+FUSED_TRAFFIC_2048_RGB = 66.40e6
+# library kernels of one fit step (profiles/launches_fit2048_rgb.md): finalize,
+# preprocess, 2 wide-Gaussian passes, 3 scan passes, emit, 2 segment sorts,
+# ranges, tile evaluations, fused adjoint, Adam
+KERNELS_PER_FIT_STEP = 14
 
 
 def fused_kernel_ops(evals, pixels, K, n):
@@ -231,7 +240,11 @@ def run_ours(args, w=WORKLOAD):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
 
     if args.kernel_once:
-        # one binning, one forward and one fused adjoint launch (for ncu captures)
+        # the fit (graph replays, as timed below), then one binning, one forward
+        # and one fused adjoint launch on the fitted state (for ncu captures)
+        for _ in range(args.steps):
+            graph.replay()
+        torch.cuda.synchronize()
         bins = L.preprocess_bin(L.packed_view(P, n), H, W, cfg, ws, cap)
         img = torch.empty((n, H, W), device=dev)
         L.render_forward(bins, cfg, img)
@@ -316,9 +329,11 @@ def run_ours(args, w=WORKLOAD):
             "gaussian_pixel_evals_per_step": evals,
             "gaussian_pixel_evals_per_s": world * evals * 1000.0 / ms,
             "final_loss": float(loss.item()),
-            "gpu_launches": 20 * args.steps,
+            "gpu_launches": KERNELS_PER_FIT_STEP * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                         "unit": "T fp32 lane-ops/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "T fp32 lane-ops/s", "frac": achieved / peak,
+                         "traffic": FUSED_TRAFFIC_2048_RGB if w["name"] == "fit2048_rgb" else None,
+                         "traffic_unit": "bytes per launch",
                          "kernel": "k_render_bwd (fused forward + L1 + adjoint)",
                          "kernel_ms": k_ms,
                          "peak_note": "148 SMs x 128 FP32 lanes x 2032 MHz (max SM clock)"},
@@ -506,7 +521,8 @@ def main():
     ap.add_argument("--workload", default="fit2048_rgb",
                     choices=list(FIT_WORKLOADS) + ["batch64", "decode8192"])
     ap.add_argument("--kernel-once", action="store_true",
-                    help="bin, render and run the fused adjoint once, then exit (profiling)")
+                    help="run the fit for --steps steps, then bin, render and run the fused "
+                         "adjoint once on the fitted state and exit (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
