@@ -349,14 +349,10 @@ __device__ __forceinline__ void culled_keys(const RenderParams& p, int cnt, floa
     const bool surv =
         lane < gw && jl < cnt && !(key_lower_bound(s_a[jl], s_b[jl].x, s_e[jl], R) > thr);
     unsigned m = __ballot_sync(FULL_MASK, surv);
-    while (m) {
-      const int j = c0 + __ffs(m) - 1;
-      m &= m - 1;
-      const float4 a = s_a[j];
-      const float q = rank_key(px, py, a.x, a.y, a.z, a.w, s_b[j].x);
+    auto take = [&](float q) {
       if (K == 0) {  // all of S_j: only the smallest key is needed
         tq[0] = fminf(tq[0], q);
-        continue;
+        return;
       }
       const bool better = q < tq[A - 1];
       float out = q;
@@ -366,6 +362,19 @@ __device__ __forceinline__ void culled_keys(const RenderParams& p, int cnt, floa
         out = better ? x : q;
       }
       mdrop = fminf(mdrop, out);
+    };
+    while (m) {
+      const int j0 = c0 + __ffs(m) - 1;
+      m &= m - 1;
+      const bool two = m != 0;
+      const int j1 = two ? c0 + __ffs(m) - 1 : j0;
+      m &= m - 1;
+      const float4 a0 = s_a[j0], a1 = s_a[j1];
+      const float b0 = s_b[j0].x, b1 = s_b[j1].x;
+      const float q0 = rank_key(px, py, a0.x, a0.y, a0.z, a0.w, b0);
+      const float q1 = rank_key(px, py, a1.x, a1.y, a1.z, a1.w, b1);
+      take(q0);
+      if (two) take(q1);
     }
     thr = warp_max_key(live ? tq[A - 1] : 0.0f);
   }
@@ -430,13 +439,8 @@ __device__ __forceinline__ void culled_blend(const RenderParams& p, int cnt, flo
     const bool surv = in && !(key_lower_bound(s_a[jl], s_b[jl].x, s_e[jl], R) > T);
     if (MASKS && in && !surv) mask_w[jl] = 0u;
     unsigned m = __ballot_sync(FULL_MASK, surv);
-    while (m) {
-      const int j = c0 + __ffs(m) - 1;
-      m &= m - 1;
-      const float4 a = s_a[j];
-      const float2 b = s_b[j];
-      const float q = rank_key(px, py, a.x, a.y, a.z, a.w, b.x);
-      const bool win = q < r.tau || (q == r.tau && __float_as_int(b.y) <= r.gcut);
+    auto take = [&](int j, float q, int gid) {
+      const bool win = q < r.tau || (q == r.tau && gid <= r.gcut);
       if (MASKS) {
         const unsigned bal = __ballot_sync(FULL_MASK, win && live);
         if (lane == 0) mask_w[j] = bal;
@@ -449,6 +453,19 @@ __device__ __forceinline__ void culled_blend(const RenderParams& p, int cnt, flo
           if (NC > 0 || c < n)
             r.cr[c] = fmaf(w, staged_colour<CH, NC>(p, s_col, s_b, j, c), r.cr[c]);
       }
+    };
+    while (m) {
+      const int j0 = c0 + __ffs(m) - 1;
+      m &= m - 1;
+      const bool two = m != 0;
+      const int j1 = two ? c0 + __ffs(m) - 1 : j0;
+      m &= m - 1;
+      const float4 a0 = s_a[j0], a1 = s_a[j1];
+      const float2 b0 = s_b[j0], b1 = s_b[j1];
+      const float q0 = rank_key(px, py, a0.x, a0.y, a0.z, a0.w, b0.x);
+      const float q1 = rank_key(px, py, a1.x, a1.y, a1.z, a1.w, b1.x);
+      take(j0, q0, __float_as_int(b0.y));
+      if (two) take(j1, q1, __float_as_int(b1.y));
     }
   }
   const float iz = p.normalize ? (r.Z > 0.0f ? 1.0f / r.Z : 0.0f) : 1.0f;
