@@ -228,15 +228,27 @@ def run_ours(args, w=WORKLOAD):
                        N, n)
     loss = torch.zeros(1, device=dev)
 
+    # Sec. 4.1 half-precision storage: float32 master, half copy rendered
+    half = None
+    if args.storage != "f32":
+        half = torch.zeros(P.shape, dtype={"f16": torch.float16, "bf16": torch.bfloat16}[
+            args.storage], device=dev)
+
+    def step_fn(stream=None):
+        if half is None:
+            L.fit_step(state, target, H, W, cfg, ws, cap, loss, stream=stream)
+        else:
+            L.fit_step_half(state, half, target, H, W, cfg, ws, cap, loss, stream=stream)
+
     s = torch.cuda.Stream(device=dev)
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
-        L.fit_step(state, target, H, W, cfg, ws, cap, loss, stream=s)
+        step_fn(stream=s)
     torch.cuda.current_stream().wait_stream(s)
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
-        L.fit_step(state, target, H, W, cfg, ws, cap, loss)
+        step_fn()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
 
     if args.kernel_once:
@@ -321,18 +333,22 @@ def run_ours(args, w=WORKLOAD):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if half is None else f"f32 math, {args.storage} parameter storage",
             "data": "synthetic",
             "config": {"workload": w["name"], "H": H, "W": W, "n": n, "N": N, "K": cfg.K,
+                       "storage": args.storage,
+                       "bits_per_pixel": N * (5 + n) * (32 if half is None else 16) / (H * W),
                        "tile": cfg.tile, "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"independent fits x{world}"},
             "gaussian_pixel_evals_per_step": evals,
             "gaussian_pixel_evals_per_s": world * evals * 1000.0 / ms,
             "final_loss": float(loss.item()),
-            "gpu_launches": KERNELS_PER_FIT_STEP * args.steps,
+            "gpu_launches": (KERNELS_PER_FIT_STEP + (0 if half is None else 2)) * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                          "unit": "T fp32 lane-ops/s", "frac": achieved / peak,
-                         "traffic": FUSED_TRAFFIC_2048_RGB if w["name"] == "fit2048_rgb" else None,
+                         "traffic": (FUSED_TRAFFIC_2048_RGB
+                                     if w["name"] == "fit2048_rgb" and half is None else None),
                          "traffic_unit": "bytes per launch",
                          "kernel": "k_render_bwd (fused forward + L1 + adjoint)",
                          "kernel_ms": k_ms,
@@ -520,6 +536,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--workload", default="fit2048_rgb",
                     choices=list(FIT_WORKLOADS) + ["batch64", "decode8192"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="parameter storage of the fit workloads (f16/bf16: half copy "
+                         "rendered, float32 master updated)")
     ap.add_argument("--kernel-once", action="store_true",
                     help="run the fit for --steps steps, then bin, render and run the fused "
                          "adjoint once on the fitted state and exit (profiling)")

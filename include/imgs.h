@@ -174,7 +174,8 @@ int igs_render_forward(const igs_bins* bins, const igs_config* cfg,
  * dL/dp. The upstream gradient is d_grad_img [n][H][W] if non-NULL;
  * otherwise L = mean |c_r - c_t| over H*W*n against d_target [n][H][W]
  * (d|z|/dz = sign(z), sign(0) = 0) and sum |c_r - c_t| is added to the
- * status block's loss_sum. Requires float32 parameters. */
+ * status block's loss_sum. The gradient is with respect to the stored
+ * parameter values (float16/bfloat16 storage: the values upcast exactly). */
 int igs_render_backward(const igs_gaussians* g, const igs_bins* bins,
                         const igs_config* cfg, const float* d_grad_img,
                         const float* d_target, float* d_grad, igs_stream stream);
@@ -206,6 +207,21 @@ int igs_adam_update(const igs_fit_state* st, const igs_config* cfg, igs_stream s
 int igs_fit_step(const igs_fit_state* st, const float* d_target, int32_t H,
                  int32_t W, const igs_config* cfg, void* ws, size_t ws_bytes,
                  int64_t m_capacity, float* d_loss_out, igs_stream stream);
+
+/* One optimisation step with half-precision parameter storage (Sec. 4.1:
+ * the Gaussians are kept in half precision, 16 bits per value): st->params
+ * is the float32 master copy; d_params_half [N][5+n] (IGS_F16 or IGS_BF16,
+ * 16-byte aligned) is the stored representation. The step rounds the master
+ * to half (nearest even), bins, renders and differentiates the half values,
+ * applies Adam to the master with that gradient, and leaves the half copy
+ * as the rounding of the updated master. Otherwise as igs_fit_step. The
+ * representation costs N (5+n) 16 / (H W) bits per pixel. This library
+ * addition has no separate counterpart in the paper beyond Sec. 4.1's
+ * storage format. */
+int igs_fit_step_half(const igs_fit_state* st, void* d_params_half, int32_t half_dtype,
+                      const float* d_target, int32_t H, int32_t W, const igs_config* cfg,
+                      void* ws, size_t ws_bytes, int64_t m_capacity, float* d_loss_out,
+                      igs_stream stream);
 
 /* Random-access decode (Sec. 2.2 / abstract: per-pixel decode): colour at
  * Q arbitrary points d_xy [Q][2] = (x, y) in pixels, written to d_out

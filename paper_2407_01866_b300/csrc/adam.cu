@@ -141,6 +141,45 @@ cudaError_t launch_adam(const AdamParams& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+namespace {
+
+// Round-to-nearest-even copy of float32 parameters into half storage.
+template <typename T>
+__global__ void __launch_bounds__(256) k_round_params(const float* src, T* dst, int64_t count);
+
+template <>
+__global__ void __launch_bounds__(256) k_round_params<__half>(const float* src, __half* dst,
+                                                              int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = __float2half_rn(src[i]);
+}
+
+template <>
+__global__ void __launch_bounds__(256) k_round_params<__nv_bfloat16>(const float* src,
+                                                                     __nv_bfloat16* dst,
+                                                                     int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+}  // namespace
+
+cudaError_t launch_round_params(const float* src, void* dst, bool bf16, int64_t count,
+                                cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  if (bf16)
+    k_round_params<__nv_bfloat16><<<(unsigned)blocks, 256, 0, s>>>(
+        src, static_cast<__nv_bfloat16*>(dst), count);
+  else
+    k_round_params<__half><<<(unsigned)blocks, 256, 0, s>>>(src, static_cast<__half*>(dst),
+                                                            count);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(int32_t* step, DevStatus* status, float inv_count, float* loss_out,
                             cudaStream_t s) {
   k_finalize<<<1, 32, 0, s>>>(step, status, inv_count, loss_out);

@@ -279,8 +279,6 @@ int igs_render_backward(const igs_gaussians* g, const igs_bins* bins, const igs_
   if (int r = check_gaussians(g)) return r;
   if (int r = check_bins(bins, cfg)) return r;
   if (int r = check_config(cfg, bins->n)) return r;
-  if (g->dtype != IGS_F32)
-    return fail(IGS_ERR_INVALID_ARG, "the adjoint needs float32 parameters");
   if (g->N != bins->N || g->n != bins->n)
     return fail(IGS_ERR_INVALID_ARG, "gaussians (N=%lld, n=%d) differ from the bins (N=%lld, n=%d)",
                 (long long)g->N, g->n, (long long)bins->N, bins->n);
@@ -366,6 +364,48 @@ int igs_fit_step(const igs_fit_state* st, const float* d_target, int32_t H, int3
   IGS_CUDA(launch_finalize(st->step, static_cast<DevStatus*>(bins.status),
                            (float)(1.0 / ((double)H * W * st->n)), d_loss_out, s),
            "finalize");
+  return IGS_OK;
+}
+
+int igs_fit_step_half(const igs_fit_state* st, void* d_params_half, int32_t half_dtype,
+                      const float* d_target, int32_t H, int32_t W, const igs_config* cfg,
+                      void* ws, size_t ws_bytes, int64_t m_capacity, float* d_loss_out,
+                      igs_stream stream) {
+  if (!st || !st->params || !st->grad || !st->adam_m || !st->adam_v || !st->step)
+    return fail(IGS_ERR_INVALID_ARG, "fit state has a NULL pointer");
+  if (!d_params_half || !d_target) return fail(IGS_ERR_INVALID_ARG, "half copy or target is NULL");
+  if (half_dtype != IGS_F16 && half_dtype != IGS_BF16)
+    return fail(IGS_ERR_INVALID_ARG, "half storage must be IGS_F16 or IGS_BF16");
+  if (!aligned(st->params, 16) || !aligned(st->grad, 16) || !aligned(st->adam_m, 16) ||
+      !aligned(st->adam_v, 16) || !aligned(d_params_half, 16) || !aligned(d_target, 4))
+    return fail(IGS_ERR_ALIGN, "fit state arrays must be 16-byte aligned");
+  if (st->N < 0 || st->n < 1 || st->n > 32)
+    return fail(IGS_ERR_INVALID_ARG, "fit state sizes out of range");
+  const int np = 5 + st->n;
+  const int64_t count = st->N * np;
+  const bool bf16 = half_dtype == IGS_BF16;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  IGS_CUDA(launch_round_params(st->params, d_params_half, bf16, count, s), "round to half");
+  uint16_t* h = static_cast<uint16_t*>(d_params_half);
+  igs_gaussians g;
+  g.xy = h;
+  g.theta = h + 2;
+  g.inv_scale = h + 3;
+  g.color = h + 5;
+  g.xy_stride = g.theta_stride = g.inv_scale_stride = g.color_stride = np;
+  g.N = st->N;
+  g.n = st->n;
+  g.dtype = half_dtype;
+  igs_bins bins;
+  if (int r = igs_preprocess_bin(&g, H, W, cfg, ws, ws_bytes, m_capacity, &bins, stream))
+    return r;
+  if (int r = igs_render_backward(&g, &bins, cfg, nullptr, d_target, st->grad, stream))
+    return r;
+  if (int r = igs_adam_update(st, cfg, stream)) return r;
+  IGS_CUDA(launch_finalize(st->step, static_cast<DevStatus*>(bins.status),
+                           (float)(1.0 / ((double)H * W * st->n)), d_loss_out, s),
+           "finalize");
+  IGS_CUDA(launch_round_params(st->params, d_params_half, bf16, count, s), "round to half");
   return IGS_OK;
 }
 

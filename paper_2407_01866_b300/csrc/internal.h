@@ -135,6 +135,9 @@ struct AdamParams {
   float theta_min, theta_max, t_min, t_max, mu_min, mu_max;
 };
 cudaError_t launch_adam(const AdamParams& a, cudaStream_t s);
+// dst[i] = float16 (or bfloat16 if bf16) rounding of src[i], nearest even.
+cudaError_t launch_round_params(const float* src, void* dst, bool bf16, int64_t count,
+                                cudaStream_t s);
 cudaError_t launch_finalize(int32_t* step, DevStatus* status, float inv_count, float* loss_out,
                             cudaStream_t s);
 // Batched form: step counter and per-image mean L1 loss.

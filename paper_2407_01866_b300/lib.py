@@ -96,6 +96,9 @@ _SIGNATURES = {
     "igs_fit_step": ([ctypes.POINTER(FitState), _P, ctypes.c_int32, ctypes.c_int32,
                       ctypes.POINTER(Config), _P, ctypes.c_size_t, ctypes.c_int64, _P, _P],
                      ctypes.c_int),
+    "igs_fit_step_half": ([ctypes.POINTER(FitState), _P, ctypes.c_int32, _P, ctypes.c_int32,
+                           ctypes.c_int32, ctypes.POINTER(Config), _P, ctypes.c_size_t,
+                           ctypes.c_int64, _P, _P], ctypes.c_int),
     "igs_adam_update": ([ctypes.POINTER(FitState), ctypes.POINTER(Config), _P], ctypes.c_int),
     "igs_decode_points": ([ctypes.POINTER(Bins), ctypes.POINTER(Config), _P, ctypes.c_int64,
                            _P, _P], ctypes.c_int),
@@ -227,6 +230,18 @@ def render_backward(g, bins, cfg, grad_img, target, grad, stream=None):
 def fit_step(state, target, H, W, cfg, ws, m_capacity, loss_out=None, stream=None):
     _check(load().igs_fit_step(ctypes.byref(state), _ptr(target), H, W, ctypes.byref(cfg),
                                _ptr(ws), ws.numel(), m_capacity, _ptr(loss_out), _stream(stream)))
+
+
+def fit_step_half(state, params_half, target, H, W, cfg, ws, m_capacity, loss_out=None,
+                  stream=None):
+    """One fit step with half-precision storage: params_half is a [N, 5+n]
+    torch.float16 or torch.bfloat16 tensor that receives the rounded master."""
+    dt = _DTYPE.get(params_half.dtype)
+    if dt not in (IGS_F16, IGS_BF16):
+        raise IgsError(IGS_ERR_INVALID_ARG, "params_half must be float16 or bfloat16")
+    _check(load().igs_fit_step_half(ctypes.byref(state), _ptr(params_half), dt, _ptr(target),
+                                    H, W, ctypes.byref(cfg), _ptr(ws), ws.numel(), m_capacity,
+                                    _ptr(loss_out), _stream(stream)))
 
 
 def adam_update(state, cfg, stream=None):

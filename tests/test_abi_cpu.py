@@ -97,3 +97,10 @@ def test_entry_points_reject_bad_arguments_without_a_gpu(lib):
         L.IGS_ERR_INVALID_ARG
     assert lib.igs_fit_step(None, None, 16, 16, ctypes.byref(c), None, 0, 1, None, None) == \
         L.IGS_ERR_INVALID_ARG
+    st = L.FitState(4096, 8192, 12288, 16384, 20480, 4, 3)
+    assert lib.igs_fit_step_half(ctypes.byref(st), ctypes.c_void_p(24576), 0, ctypes.c_void_p(28672),
+                                 16, 16, ctypes.byref(c), None, 0, 1, None, None) == \
+        L.IGS_ERR_INVALID_ARG   # float32 is not a half storage type
+    assert lib.igs_fit_step_half(ctypes.byref(st), ctypes.c_void_p(24576 + 2), 1,
+                                 ctypes.c_void_p(28672), 16, 16, ctypes.byref(c), None, 0, 1,
+                                 None, None) == L.IGS_ERR_ALIGN

@@ -148,3 +148,37 @@ def test_fit_loss_decreases_and_graph_replay_matches_eager():
     # warm-up ran once, capture runs nothing, each replay runs one step
     assert int(st_g.step.item()) == 5
     np.testing.assert_allclose(glosses, losses[:5], rtol=1e-3)
+
+
+@pytest.mark.parametrize("dt", [torch.float16, torch.bfloat16])
+def test_half_storage_fit_step_matches_oracle_step(dt):
+    """Sec. 4.1 half-precision storage: the step renders and differentiates the
+    half-rounded parameters, and Adam updates the float32 master."""
+    H, W, N, n = 96, 80, 800, 3
+    P = synth.packed(synth.gaussians(N, n, 5))
+    Pr16 = torch.from_numpy(P).to(dt).float().numpy()        # the stored values
+    g = O.Gaussians.from_packed(Pr16)
+    target, img = _unambiguous_target(g, H, W, 6)
+    cfg = L.default_config()
+    st = State(P)
+    half = torch.zeros(P.shape, dtype=dt, device="cuda")
+    ws = L.alloc_workspace(L.workspace_size(N, n, H, W, cfg, 8 * N))
+    loss = torch.zeros(1, device="cuda")
+    L.fit_step_half(st.c, half, dev(target), H, W, cfg, ws, 8 * N, loss)
+    torch.cuda.synchronize()
+    ref_loss, dimg = O.l1_loss(img, target)
+    ref_grad = O.backward_image(g, dimg, H, W)
+    assert abs(loss.item() - ref_loss) <= 1e-6
+    assert int(st.step.item()) == 1
+    errs = grad_rel_error(st.G.cpu().numpy().astype(np.float64), ref_grad)
+    assert max(errs.values()) <= 1e-3, errs
+    # the master moves by Adam step 1 from its own float32 values
+    Pr, _, _ = O.adam_update(P, ref_grad, np.zeros(P.shape), np.zeros(P.shape), 1)
+    lr = lr_of(cfg, P.shape[1])[None, :]
+    dg = 1e-3 * np.abs(ref_grad).max(axis=0, keepdims=True)
+    bound = np.minimum(2 * lr, lr * 1e-8 * dg / (np.abs(ref_grad) + 1e-8) ** 2 + 1e-6 * lr)
+    bound = bound + 2e-6 * np.abs(Pr) + 1e-7
+    got = st.P.cpu().numpy()
+    assert (np.abs(got - Pr) <= bound).all()
+    # the stored copy is the nearest-even rounding of the updated master
+    assert torch.equal(half.cpu(), st.P.cpu().to(dt))
