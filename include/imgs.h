@@ -313,6 +313,42 @@ int igs_render_forward_static(const igs_gaussians* g, int32_t H, int32_t W,
 /* Size in bytes of the static scratch used by igs_render_forward_static. */
 int igs_static_scratch_bytes(size_t* bytes);
 
+/* Content-adaptive placement (Sec. 3.3). Both draws are independent and
+ * decided exactly, so that they can be reproduced bit for bit:
+ *   weights   binary32: Eq. 6 uses |grad I|_2 with, per channel, central
+ *             differences (I[k+1] - I[k-1]) * 0.5 inside and one-sided
+ *             differences at the borders (0 along an axis of length 1),
+ *             accumulated s += gx*gx, s += gy*gy over channels, then sqrt;
+ *             Eq. 7 uses the sum over channels of |c_r - c_t|
+ *   integers  floor(min(w, 4096) * 2^24), non-finite -> 0; exclusive prefix
+ *             sums give a 64-bit cumulative weight
+ *   draw      from 53-bit integers r1, r2 (u = r / 2^53; the top 11 bits of the
+ *             inputs are ignored): if r1 < floor(lambda * 2^53) or every weight
+ *             is 0, pixel floor(r2 * H * W / 2^53); otherwise the last pixel
+ *             whose exclusive prefix is <= floor(r2 * total / 2^53)
+ *   Gaussian  mu = ((x + 0.5) / W, (y + 0.5) / H) in binary32, theta = 0,
+ *             t = (0.2, 0.2) (5 px, Sec. 4.1), colour = the target at the pixel
+ * Scratch: a device workspace of igs_placement_workspace_size() bytes,
+ * 256-byte aligned. */
+int igs_placement_workspace_size(int32_t H, int32_t W, size_t* bytes);
+
+/* Eq. 6: N initial Gaussians drawn from the target d_target [n][H][W] with
+ * uniform share lambda in [0, 1] (Sec. 4.1: 0.3). d_rand [N][2] holds (r1,
+ * r2) per Gaussian; d_params [N][5+n] receives the packed rows. */
+int igs_init_gaussians(const float* d_target, int32_t H, int32_t W, int32_t n, int64_t N,
+                       double lambda, const uint64_t* d_rand, float* d_params, void* ws,
+                       size_t ws_bytes, igs_stream stream);
+
+/* Eq. 7: `count` Gaussians added where the rendering d_render [n][H][W]
+ * (igs_render_forward of the current parameters) differs from d_target.
+ * d_rand [count][2] (r1 is ignored). Writes rows [st->N, st->N + count) of
+ * st->params and zeroes those rows of st->grad, st->adam_m and st->adam_v; the
+ * arrays must have room for them, and the caller then raises N by count
+ * (Sec. 4.1 starts from N/2 and adds N/8 every 500 steps). */
+int igs_add_gaussians(const float* d_target, const float* d_render, int32_t H, int32_t W,
+                      const uint64_t* d_rand, int64_t count, const igs_fit_state* st,
+                      void* ws, size_t ws_bytes, igs_stream stream);
+
 /* Synchronously copies the workspace's status block to *out (this call
  * synchronises `stream`). */
 int igs_read_stats(const igs_bins* bins, igs_stats* out, igs_stream stream);

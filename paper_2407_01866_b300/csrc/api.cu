@@ -426,6 +426,57 @@ int igs_decode_points(const igs_bins* bins, const igs_config* cfg, const float* 
   return IGS_OK;
 }
 
+int igs_placement_workspace_size(int32_t H, int32_t W, size_t* bytes) {
+  if (!bytes) return fail(IGS_ERR_INVALID_ARG, "bytes is NULL");
+  if (H < 1 || W < 1) return fail(IGS_ERR_INVALID_ARG, "image size must be positive");
+  *bytes = place_layout((int64_t)H * W).bytes;
+  return IGS_OK;
+}
+
+static int check_place(const float* d_target, int32_t H, int32_t W, int32_t n,
+                       const uint64_t* d_rand, int64_t count, void* ws, size_t ws_bytes) {
+  if (H < 1 || W < 1 || n < 1 || n > 32 || count < 0)
+    return fail(IGS_ERR_INVALID_ARG, "sizes out of range");
+  if (!d_target || !ws || (count > 0 && !d_rand))
+    return fail(IGS_ERR_INVALID_ARG, "target, workspace or random numbers NULL");
+  if (!aligned(d_target, 4) || !aligned(d_rand, 8) || !aligned(ws, 256))
+    return fail(IGS_ERR_ALIGN, "target 4-, random numbers 8-, workspace 256-byte aligned");
+  if (ws_bytes < place_layout((int64_t)H * W).bytes)
+    return fail(IGS_ERR_INVALID_ARG, "placement workspace too small");
+  return IGS_OK;
+}
+
+int igs_init_gaussians(const float* d_target, int32_t H, int32_t W, int32_t n, int64_t N,
+                       double lambda, const uint64_t* d_rand, float* d_params, void* ws,
+                       size_t ws_bytes, igs_stream stream) {
+  if (int r = check_place(d_target, H, W, n, d_rand, N, ws, ws_bytes)) return r;
+  if (!(lambda >= 0.0 && lambda <= 1.0)) return fail(IGS_ERR_INVALID_ARG, "lambda not in [0, 1]");
+  if (N > 0 && !d_params) return fail(IGS_ERR_INVALID_ARG, "params NULL");
+  if (!aligned(d_params, 4)) return fail(IGS_ERR_ALIGN, "params must be 4-byte aligned");
+  IGS_CUDA(launch_place(d_target, nullptr, H, W, n,
+                        reinterpret_cast<const unsigned long long*>(d_rand), N, lambda, d_params,
+                        0, nullptr, nullptr, nullptr, static_cast<char*>(ws),
+                        reinterpret_cast<cudaStream_t>(stream)),
+           "init gaussians");
+  return IGS_OK;
+}
+
+int igs_add_gaussians(const float* d_target, const float* d_render, int32_t H, int32_t W,
+                      const uint64_t* d_rand, int64_t count, const igs_fit_state* st, void* ws,
+                      size_t ws_bytes, igs_stream stream) {
+  if (!st || !st->params || !st->grad || !st->adam_m || !st->adam_v)
+    return fail(IGS_ERR_INVALID_ARG, "fit state has a NULL pointer");
+  if (int r = check_place(d_target, H, W, st->n, d_rand, count, ws, ws_bytes)) return r;
+  if (!d_render) return fail(IGS_ERR_INVALID_ARG, "render is NULL");
+  if (!aligned(d_render, 4)) return fail(IGS_ERR_ALIGN, "render must be 4-byte aligned");
+  IGS_CUDA(launch_place(d_target, d_render, H, W, st->n,
+                        reinterpret_cast<const unsigned long long*>(d_rand), count, 0.0,
+                        st->params, st->N, st->grad, st->adam_m, st->adam_v,
+                        static_cast<char*>(ws), reinterpret_cast<cudaStream_t>(stream)),
+           "add gaussians");
+  return IGS_OK;
+}
+
 int igs_read_stats(const igs_bins* bins, igs_stats* out, igs_stream stream) {
   if (!bins || !bins->status || !out) return fail(IGS_ERR_INVALID_ARG, "NULL argument");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -549,6 +549,12 @@ cudaError_t launch_scan_u32_to_u64(const unsigned int* in, unsigned long long* o
   return scan_exclusive<unsigned int, unsigned long long>(in, out, n, part, total, s);
 }
 
+cudaError_t launch_scan_u64(const unsigned long long* in, unsigned long long* out, int64_t n,
+                            unsigned long long* part, unsigned long long* total,
+                            cudaStream_t s) {
+  return scan_exclusive<unsigned long long, unsigned long long>(in, out, n, part, total, s);
+}
+
 cudaError_t run_binning(const PrepParams& p, int dtype, int T, unsigned long long* part,
                         int2* range, int sort_min, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(p.tcnt, 0, sizeof(unsigned int) * (size_t)T, s);

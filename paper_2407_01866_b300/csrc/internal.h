@@ -135,6 +135,25 @@ struct AdamParams {
   float theta_min, theta_max, t_min, t_max, mu_min, mu_max;
 };
 cudaError_t launch_adam(const AdamParams& a, cudaStream_t s);
+
+// Content-adaptive placement (Sec. 3.3, Eq. 6 / Eq. 7): workspace sections
+// (bytes, 256-aligned) for an image of HW pixels.
+struct PlaceLayout {
+  size_t weights, excl, part, total, bytes;
+};
+PlaceLayout place_layout(int64_t HW);
+// Draws `count` pixels (render == nullptr: Eq. 6 from the target's gradient
+// magnitudes with uniform share lambda; otherwise Eq. 7 from |render - target|)
+// and writes new Gaussians to rows [row0, row0 + count) of params; zeroes those
+// rows of grad, m, v when grad is non-null. rnd holds 2 * count 53-bit integers.
+cudaError_t launch_place(const float* target, const float* render, int H, int W, int n,
+                         const unsigned long long* rnd, int64_t count, double lambda,
+                         float* params, int64_t row0, float* grad, float* m, float* v,
+                         char* ws, cudaStream_t s);
+// Exclusive prefix sum of 64-bit integers; *total receives the sum.
+cudaError_t launch_scan_u64(const unsigned long long* in, unsigned long long* out, int64_t n,
+                            unsigned long long* part, unsigned long long* total,
+                            cudaStream_t s);
 // dst[i] = float16 (or bfloat16 if bf16) rounding of src[i], nearest even.
 cudaError_t launch_round_params(const float* src, void* dst, bool bf16, int64_t count,
                                 cudaStream_t s);

@@ -100,6 +100,12 @@ _SIGNATURES = {
                            ctypes.c_int32, ctypes.POINTER(Config), _P, ctypes.c_size_t,
                            ctypes.c_int64, _P, _P], ctypes.c_int),
     "igs_adam_update": ([ctypes.POINTER(FitState), ctypes.POINTER(Config), _P], ctypes.c_int),
+    "igs_placement_workspace_size": ([ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "igs_init_gaussians": ([_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                            ctypes.c_double, _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
+    "igs_add_gaussians": ([_P, _P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int64,
+                           ctypes.POINTER(FitState), _P, ctypes.c_size_t, _P], ctypes.c_int),
     "igs_decode_points": ([ctypes.POINTER(Bins), ctypes.POINTER(Config), _P, ctypes.c_int64,
                            _P, _P], ctypes.c_int),
     "igs_read_stats": ([ctypes.POINTER(Bins), ctypes.POINTER(Stats), _P], ctypes.c_int),
@@ -242,6 +248,28 @@ def fit_step_half(state, params_half, target, H, W, cfg, ws, m_capacity, loss_ou
     _check(load().igs_fit_step_half(ctypes.byref(state), _ptr(params_half), dt, _ptr(target),
                                     H, W, ctypes.byref(cfg), _ptr(ws), ws.numel(), m_capacity,
                                     _ptr(loss_out), _stream(stream)))
+
+
+def placement_workspace_size(H, W):
+    b = ctypes.c_size_t()
+    _check(load().igs_placement_workspace_size(H, W, ctypes.byref(b)))
+    return b.value
+
+
+def init_gaussians(target, N, rand, params, ws, lam=0.3, stream=None):
+    """Eq. 6 placement: target [n, H, W] float32, rand [N, 2] int64 (53-bit
+    values), params [N, 5+n] float32 output."""
+    n, H, W = target.shape
+    _check(load().igs_init_gaussians(_ptr(target), H, W, n, N, lam, _ptr(rand), _ptr(params),
+                                     _ptr(ws), ws.numel(), _stream(stream)))
+
+
+def add_gaussians(target, render, rand, count, state, ws, stream=None):
+    """Eq. 7 placement of `count` Gaussians after row state.N (the caller raises
+    state.N afterwards)."""
+    n, H, W = target.shape
+    _check(load().igs_add_gaussians(_ptr(target), _ptr(render), H, W, _ptr(rand), count,
+                                    ctypes.byref(state), _ptr(ws), ws.numel(), _stream(stream)))
 
 
 def adam_update(state, cfg, stream=None):

@@ -1,0 +1,92 @@
+"""Content-adaptive placement (Sec. 3.3, Eq. 6 and Eq. 7) through the C ABI.
+
+The draws are integer results decided exactly on both sides, so the new
+Gaussians must equal the oracle's bit for bit. The "rendering" of Eq. 7 is
+any image; here it is a seeded synthetic one (no oracle input comes from
+the CUDA path).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import placement as PL  # noqa: E402
+from paper_2407_01866_b300 import lib as L  # noqa: E402
+from paper_2407_01866_b300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from gpu_harness import dev  # noqa: E402
+
+R53 = 2 ** 53
+
+
+def _rand(count, seed):
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, R53, (count, 2), dtype=np.int64)
+
+
+def _ws(H, W):
+    return L.alloc_workspace(L.placement_workspace_size(H, W))
+
+
+@pytest.mark.parametrize("H,W,n,N,lam,seed", [
+    (160, 120, 3, 5000, 0.3, 0),
+    (37, 53, 1, 700, 0.0, 1),       # weighted part only, ragged size
+    (64, 64, 9, 300, 1.0, 2),       # uniform part only
+    (1, 40, 3, 100, 0.3, 3),        # a single row
+])
+def test_init_gaussians_equal_oracle(H, W, n, N, lam, seed):
+    target = synth.target_image(H, W, n, seed=seed)
+    rnd = _rand(N, seed + 10)
+    out = torch.zeros((N, 5 + n), device="cuda")
+    L.init_gaussians(dev(target), N, torch.from_numpy(rnd).cuda(), out, _ws(H, W), lam=lam)
+    want = PL.init_gaussians(target, rnd[:, 0], rnd[:, 1], lam=lam)
+    np.testing.assert_array_equal(out.cpu().numpy(), want)
+
+
+def test_init_on_a_flat_target_is_uniform_and_equals_oracle():
+    H, W, n, N = 32, 48, 3, 2000
+    target = np.full((n, H, W), 0.25, np.float32)
+    rnd = _rand(N, 20)
+    out = torch.zeros((N, 5 + n), device="cuda")
+    L.init_gaussians(dev(target), N, torch.from_numpy(rnd).cuda(), out, _ws(H, W))
+    np.testing.assert_array_equal(out.cpu().numpy(), PL.init_gaussians(target, rnd[:, 0], rnd[:, 1]))
+
+
+def test_add_gaussians_equal_oracle_and_reset_their_optimiser_state():
+    H, W, n = 96, 80, 3
+    N0, add = 1000, 400
+    target = synth.target_image(H, W, n, seed=5)
+    render = synth.target_image(H, W, n, seed=6)
+    P0 = synth.packed(synth.gaussians(N0, n, 7))
+    P = torch.zeros((N0 + add, 5 + n), device="cuda")
+    P[:N0] = dev(P0)
+    G = torch.full_like(P, 3.0)
+    m = torch.full_like(P, 4.0)
+    v = torch.full_like(P, 5.0)
+    step = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = L.FitState(P.data_ptr(), G.data_ptr(), m.data_ptr(), v.data_ptr(), step.data_ptr(),
+                    N0, n)
+    rnd = _rand(add, 8)
+    L.add_gaussians(dev(target), dev(render), torch.from_numpy(rnd).cuda(), add, st, _ws(H, W))
+    got = P.cpu().numpy()
+    np.testing.assert_array_equal(got[:N0], P0)
+    np.testing.assert_array_equal(got[N0:], PL.add_gaussians(target, render, rnd[:, 1]))
+    for a, fill in ((G, 3.0), (m, 4.0), (v, 5.0)):
+        a = a.cpu().numpy()
+        assert np.all(a[:N0] == fill) and np.all(a[N0:] == 0.0)
+
+
+def test_fullsize_init_2048_equals_oracle():
+    H = W = 2048
+    n, N = 3, 50_000
+    target = synth.target_image(H, W, n, seed=0, n_sin=8, n_rect=200, noise_octaves=3)
+    rnd = _rand(N, 30)
+    out = torch.zeros((N, 5 + n), device="cuda")
+    L.init_gaussians(dev(target), N, torch.from_numpy(rnd).cuda(), out, _ws(H, W))
+    np.testing.assert_array_equal(out.cpu().numpy(),
+                                  PL.init_gaussians(target, rnd[:, 0], rnd[:, 1]))
