@@ -7,6 +7,7 @@ CPU fallback: if the library is missing or cannot be loaded, every call raises.
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -400,3 +401,113 @@ class _RenderFn(torch.autograd.Function):
 def render(xy, theta, inv_scale, color, H, W, cfg=None):
     """Differentiable render (Eq. 5) -> planar float32 [n, H, W]."""
     return _RenderFn.apply(xy, theta, inv_scale, color, H, W, cfg or default_config())
+
+
+class Fitter:
+    """The fitting schedule of Sec. 4.1 on one target, through the C ABI.
+
+    It starts with N/2 Gaussians placed by Eq. 6 (gradient-guided, uniform
+    share `lam`), then runs fit steps (`igs_fit_step`, or `igs_fit_step_half`
+    with `storage` 'f16'/'bf16'). Every `add_every` steps it adds N/8
+    Gaussians placed by Eq. 7 on the current rendering, until the budget N is
+    reached. Buffers are sized for N up front. `graphs=True` replays each step
+    from a CUDA graph captured per Gaussian count. The random numbers of the
+    draws come from numpy's generator seeded with `seed`.
+    """
+
+    R53 = 1 << 53
+
+    def __init__(self, target, N, cfg=None, lam=0.3, seed=0, start_frac=0.5, add_frac=0.125,
+                 add_every=500, storage="f32", graphs=False, m_capacity=None):
+        self.target = target.contiguous().float()
+        self.n, self.H, self.W = self.target.shape
+        self.budget = int(N)
+        self.cfg = cfg or default_config()
+        self.add_n = max(1, int(round(add_frac * N)))
+        self.add_every = int(add_every)
+        self.rng = np.random.default_rng(seed)
+        dev = self.target.device
+        np_ = 5 + self.n
+        self.P = torch.zeros((N, np_), device=dev)
+        self.G = torch.zeros_like(self.P)
+        self.m = torch.zeros_like(self.P)
+        self.v = torch.zeros_like(self.P)
+        self.step_ctr = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.loss = torch.zeros(1, device=dev)
+        self.half = None
+        if storage != "f32":
+            self.half = torch.zeros((N, np_), dtype={"f16": torch.float16,
+                                                      "bf16": torch.bfloat16}[storage],
+                                    device=dev)
+        self.m_capacity = int(m_capacity or 16 * N + 4096)
+        self.ws = alloc_workspace(workspace_size(N, self.n, self.H, self.W, self.cfg,
+                                                 self.m_capacity), dev)
+        self.pws = alloc_workspace(placement_workspace_size(self.H, self.W), dev)
+        n0 = max(1, int(round(start_frac * N)))
+        init_gaussians(self.target, n0, self._rand(n0), self.P, self.pws, lam=lam)
+        self.state = FitState(self.P.data_ptr(), self.G.data_ptr(), self.m.data_ptr(),
+                              self.v.data_ptr(), self.step_ctr.data_ptr(), n0, self.n)
+        self.steps = 0
+        self.graphs = graphs
+        self._graph = None
+        self._graph_n = -1
+
+    def _rand(self, count):
+        r = self.rng.integers(0, self.R53, (count, 2), dtype=np.int64)
+        return torch.from_numpy(r).to(self.target.device)
+
+    @property
+    def N(self):
+        return int(self.state.N)
+
+    @property
+    def params(self):
+        return self.P[:self.N]
+
+    def _one_step(self, stream=None):
+        if self.half is None:
+            fit_step(self.state, self.target, self.H, self.W, self.cfg, self.ws, self.m_capacity,
+                     self.loss, stream=stream)
+        else:
+            fit_step_half(self.state, self.half, self.target, self.H, self.W, self.cfg, self.ws,
+                          self.m_capacity, self.loss, stream=stream)
+
+    def step(self):
+        """One fit step (and the scheduled addition after it); returns the loss tensor."""
+        if self.graphs:
+            if self._graph_n != self.N:
+                s = torch.cuda.Stream(device=self.target.device)
+                s.wait_stream(torch.cuda.current_stream())
+                with torch.cuda.stream(s):
+                    self._one_step(stream=s)     # this is the step itself
+                torch.cuda.current_stream().wait_stream(s)
+                self._graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(self._graph):   # recorded, not run
+                    self._one_step()
+                self._graph_n = self.N
+            else:
+                self._graph.replay()
+        else:
+            self._one_step()
+        self.steps += 1
+        if self.add_every > 0 and self.steps % self.add_every == 0 and self.N < self.budget:
+            self.add()
+        return self.loss
+
+    def render(self):
+        """The current image [n, H, W] (from the stored parameters)."""
+        src = self.params if self.half is None else self.half[:self.N]
+        view = packed_view(src, self.n)
+        bins = preprocess_bin(view, self.H, self.W, self.cfg, self.ws, self.m_capacity)
+        img = torch.empty((self.n, self.H, self.W), device=self.target.device)
+        render_forward(bins, self.cfg, img)
+        return img
+
+    def add(self):
+        """Eq. 7: add min(N/8, room) Gaussians where the rendering errs most."""
+        count = min(self.add_n, self.budget - self.N)
+        if count <= 0:
+            return
+        img = self.render()
+        add_gaussians(self.target, img, self._rand(count), count, self.state, self.pws)
+        self.state.N = self.N + count

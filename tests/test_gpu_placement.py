@@ -90,3 +90,26 @@ def test_fullsize_init_2048_equals_oracle():
     L.init_gaussians(dev(target), N, torch.from_numpy(rnd).cuda(), out, _ws(H, W))
     np.testing.assert_array_equal(out.cpu().numpy(),
                                   PL.init_gaussians(target, rnd[:, 0], rnd[:, 1]))
+
+
+def test_fitter_schedule_grows_to_the_budget_and_lowers_the_loss():
+    H, W, n, N = 128, 96, 3, 800
+    target = dev(synth.target_image(H, W, n, seed=9))
+    fit = L.Fitter(target, N, add_every=20, seed=1)
+    assert fit.N == 400
+    first = fit.step().item()
+    for _ in range(99):
+        loss = fit.step()
+    assert fit.N == N                      # 400 + 4 x 100
+    assert loss.item() < 0.7 * first
+    img = fit.render()
+    assert torch.isfinite(img).all()
+    # graph replay follows the same trajectory as eager steps
+    a = L.Fitter(target, N, add_every=10, seed=2)
+    b = L.Fitter(target, N, add_every=10, seed=2, graphs=True)
+    for _ in range(25):
+        la, lb = a.step().item(), b.step().item()
+    assert a.N == b.N == 600
+    # the adjoint's float atomics add in no fixed order: equal up to rounding
+    assert abs(la - lb) <= 1e-4 * max(1.0, abs(la))
+    torch.testing.assert_close(a.params, b.params, rtol=1e-4, atol=1e-4)
