@@ -104,6 +104,11 @@ typedef struct {
   float eps;
   /* clamps after each update (Sec. 3.1): theta, inverse scale, mean */
   float theta_min, theta_max, t_min, t_max, mu_min, mu_max;
+  /* weight w of the SSIM term of the fit loss L1 + w L_SSIM (Sec. 4.1:
+   * 0.1). 0 (default) fits against L1 alone with the fused adjoint; w > 0
+   * runs forward render, igs_image_loss and the adjoint with that upstream
+   * gradient, and needs the larger workspace igs_workspace_size reports */
+  float ssim_weight;
 } igs_config;
 
 /* Host-readable copy of the device status block of one workspace. */
@@ -312,6 +317,19 @@ int igs_render_forward_static(const igs_gaussians* g, int32_t H, int32_t W,
 
 /* Size in bytes of the static scratch used by igs_render_forward_static. */
 int igs_static_scratch_bytes(size_t* bytes);
+
+/* Image-space fitting loss (Sec. 3.3, Sec. 4.1: L1 + 0.1 L_SSIM) of a
+ * rendering d_render against d_target ([n][H][W] float32 each):
+ * L = mean |x - y| + w (1 - mean SSIM), means over channels and pixels,
+ * d|z|/dz = sign(z) with sign(0) = 0. SSIM per channel with an 11 x 11
+ * Gaussian window (sigma 1.5, normalised, zero-padded "same" correlation),
+ * C1 = 0.01^2, C2 = 0.03^2 (data range 1). d_grad_img [n][H][W] receives
+ * dL/dx; d_loss_out (nullable, device float) the loss. float32 arithmetic.
+ * Scratch: igs_image_loss_workspace_size() bytes, 256-byte aligned. */
+int igs_image_loss_workspace_size(int32_t n, int32_t H, int32_t W, size_t* bytes);
+int igs_image_loss(const float* d_render, const float* d_target, int32_t n, int32_t H,
+                   int32_t W, float ssim_weight, float* d_grad_img, float* d_loss_out,
+                   void* ws, size_t ws_bytes, igs_stream stream);
 
 /* Content-adaptive placement (Sec. 3.3). Both draws are independent and
  * decided exactly, so that they can be reproduced bit for bit:

@@ -73,6 +73,8 @@ WsLayout ws_layout_tiles(int64_t N, int n, int64_t T, int64_t m_cap) {
 
 static int check_config(const igs_config* cfg, int n) {
   if (!cfg) return fail(IGS_ERR_INVALID_ARG, "config is NULL");
+  if (!(cfg->ssim_weight >= 0.0f && cfg->ssim_weight <= 1e6f))
+    return fail(IGS_ERR_INVALID_ARG, "ssim_weight must be finite and >= 0");
   if (cfg->normalize != 0 && cfg->normalize != 1)
     return fail(IGS_ERR_INVALID_ARG, "normalize must be 0 or 1");
   if (!render_supported(cfg->tile, cfg->K, n))
@@ -157,6 +159,34 @@ int igs_last_error(char* buf, size_t n) {
   return (int)s.size();
 }
 
+// Extra workspace of a fit step with the SSIM term, after the binning
+// sections: the rendering, its image-space gradient and the loss scratch.
+static size_t fit_extra_bytes(const igs_config* cfg, int n, int H, int W) {
+  if (!(cfg->ssim_weight > 0.0f)) return 0;
+  const size_t img = align_up(sizeof(float) * (size_t)n * H * W, 256);
+  return 2 * img + image_loss_scratch_bytes(n, H, W);
+}
+
+// The fit step's loss and adjoint: the fused L1 adjoint, or (SSIM term) forward
+// render, image loss and the adjoint of its image-space gradient.
+static int fit_loss_adjoint(const igs_gaussians* g, const igs_bins* bins, const igs_config* cfg,
+                            const float* d_target, float* d_grad, char* base, size_t binning_bytes,
+                            igs_stream stream) {
+  if (!(cfg->ssim_weight > 0.0f))
+    return igs_render_backward(g, bins, cfg, nullptr, d_target, d_grad, stream);
+  const int n = bins->n, H = bins->H, W = bins->W;
+  const size_t img_bytes = align_up(sizeof(float) * (size_t)n * H * W, 256);
+  float* img = reinterpret_cast<float*>(base + binning_bytes);
+  float* gimg = reinterpret_cast<float*>(base + binning_bytes + img_bytes);
+  char* scratch = base + binning_bytes + 2 * img_bytes;
+  if (int r = igs_render_forward(bins, cfg, img, stream)) return r;
+  IGS_CUDA(launch_image_loss(img, d_target, n, H, W, cfg->ssim_weight, gimg,
+                             &static_cast<DevStatus*>(bins->status)->loss_sum, nullptr, scratch,
+                             reinterpret_cast<cudaStream_t>(stream)),
+           "image loss");
+  return igs_render_backward(g, bins, cfg, gimg, nullptr, d_grad, stream);
+}
+
 void igs_default_config(igs_config* c) {
   if (!c) return;
   c->K = 10;
@@ -175,6 +205,7 @@ void igs_default_config(igs_config* c) {
   c->t_max = 10.0f;
   c->mu_min = 0.0f;
   c->mu_max = 1.0f;
+  c->ssim_weight = 0.0f;
 }
 
 int igs_workspace_size(int64_t N, int32_t n, int32_t H, int32_t W, const igs_config* cfg,
@@ -184,7 +215,7 @@ int igs_workspace_size(int64_t N, int32_t n, int32_t H, int32_t W, const igs_con
   if (int r = check_image(H, W)) return r;
   if (N < 0 || m_capacity < 1 || m_capacity > (int64_t)INT32_MAX)
     return fail(IGS_ERR_INVALID_ARG, "N or m_capacity out of range");
-  *bytes = ws_layout(N, n, H, W, cfg->tile, m_capacity).total;
+  *bytes = ws_layout(N, n, H, W, cfg->tile, m_capacity).total + fit_extra_bytes(cfg, n, H, W);
   return IGS_OK;
 }
 
@@ -357,7 +388,11 @@ int igs_fit_step(const igs_fit_state* st, const float* d_target, int32_t H, int3
   igs_bins bins;
   if (int r = igs_preprocess_bin(&g, H, W, cfg, ws, ws_bytes, m_capacity, &bins, stream))
     return r;
-  if (int r = igs_render_backward(&g, &bins, cfg, nullptr, d_target, st->grad, stream))
+  const size_t binning_bytes = ws_layout(st->N, st->n, H, W, cfg->tile, m_capacity).total;
+  if (ws_bytes < binning_bytes + fit_extra_bytes(cfg, st->n, H, W))
+    return fail(IGS_ERR_INVALID_ARG, "workspace too small for the SSIM term");
+  if (int r = fit_loss_adjoint(&g, &bins, cfg, d_target, st->grad, static_cast<char*>(ws),
+                               binning_bytes, stream))
     return r;
   if (int r = igs_adam_update(st, cfg, stream)) return r;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -399,7 +434,11 @@ int igs_fit_step_half(const igs_fit_state* st, void* d_params_half, int32_t half
   igs_bins bins;
   if (int r = igs_preprocess_bin(&g, H, W, cfg, ws, ws_bytes, m_capacity, &bins, stream))
     return r;
-  if (int r = igs_render_backward(&g, &bins, cfg, nullptr, d_target, st->grad, stream))
+  const size_t binning_bytes = ws_layout(st->N, st->n, H, W, cfg->tile, m_capacity).total;
+  if (ws_bytes < binning_bytes + fit_extra_bytes(cfg, st->n, H, W))
+    return fail(IGS_ERR_INVALID_ARG, "workspace too small for the SSIM term");
+  if (int r = fit_loss_adjoint(&g, &bins, cfg, d_target, st->grad, static_cast<char*>(ws),
+                               binning_bytes, stream))
     return r;
   if (int r = igs_adam_update(st, cfg, stream)) return r;
   IGS_CUDA(launch_finalize(st->step, static_cast<DevStatus*>(bins.status),
@@ -423,6 +462,34 @@ int igs_decode_points(const igs_bins* bins, const igs_config* cfg, const float* 
   p.qout = d_out;
   p.Q = Q;
   IGS_CUDA(launch_decode(p, cfg->K, reinterpret_cast<cudaStream_t>(stream)), "decode");
+  return IGS_OK;
+}
+
+int igs_image_loss_workspace_size(int32_t n, int32_t H, int32_t W, size_t* bytes) {
+  if (!bytes) return fail(IGS_ERR_INVALID_ARG, "bytes is NULL");
+  if (n < 1 || H < 1 || W < 1) return fail(IGS_ERR_INVALID_ARG, "sizes must be positive");
+  *bytes = 256 + image_loss_scratch_bytes(n, H, W);
+  return IGS_OK;
+}
+
+int igs_image_loss(const float* d_render, const float* d_target, int32_t n, int32_t H,
+                   int32_t W, float ssim_weight, float* d_grad_img, float* d_loss_out,
+                   void* ws, size_t ws_bytes, igs_stream stream) {
+  if (n < 1 || H < 1 || W < 1) return fail(IGS_ERR_INVALID_ARG, "sizes must be positive");
+  if (!d_render || !d_target || !d_grad_img || !ws)
+    return fail(IGS_ERR_INVALID_ARG, "render, target, gradient or workspace NULL");
+  if (!(ssim_weight >= 0.0f && ssim_weight <= 1e6f))
+    return fail(IGS_ERR_INVALID_ARG, "ssim_weight must be finite and >= 0");
+  if (!aligned(d_render, 4) || !aligned(d_target, 4) || !aligned(d_grad_img, 4) ||
+      !aligned(d_loss_out, 4) || !aligned(ws, 256))
+    return fail(IGS_ERR_ALIGN, "arrays 4-byte, workspace 256-byte aligned");
+  if (ws_bytes < 256 + image_loss_scratch_bytes(n, H, W))
+    return fail(IGS_ERR_INVALID_ARG, "image-loss workspace too small");
+  char* base = static_cast<char*>(ws);
+  IGS_CUDA(launch_image_loss(d_render, d_target, n, H, W, ssim_weight, d_grad_img,
+                             reinterpret_cast<double*>(base), d_loss_out, base + 256,
+                             reinterpret_cast<cudaStream_t>(stream)),
+           "image loss");
   return IGS_OK;
 }
 

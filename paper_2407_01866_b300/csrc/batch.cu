@@ -44,6 +44,8 @@ int bfail(int code, const char* fmt, ...) {
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
 int batch_geom(const igs_batch_shape* sh, const igs_config* cfg, int64_t m_cap, BatchGeom* G) {
+  if (cfg && cfg->ssim_weight > 0.0f)
+    return bfail(IGS_ERR_INVALID_ARG, "batch: the SSIM term is not supported (L1 only)");
   if (!sh || !cfg) return bfail(IGS_ERR_INVALID_ARG, "batch: NULL shape or config");
   if (sh->B < 1 || !sh->H || !sh->W || !sh->N)
     return bfail(IGS_ERR_INVALID_ARG, "batch: B < 1 or a NULL size array");

@@ -150,6 +150,14 @@ cudaError_t launch_place(const float* target, const float* render, int H, int W,
                          const unsigned long long* rnd, int64_t count, double lambda,
                          float* params, int64_t row0, float* grad, float* m, float* v,
                          char* ws, cudaStream_t s);
+// Image-space loss L1 + w (1 - SSIM) (Sec. 4.1) of rendering x against
+// target y ([n][H][W] each): d_grad receives dL/dx, *acc (zeroed here) the
+// sum over channels and pixels of |x - y| + w (1 - S), loss_out (nullable)
+// the mean. scratch: image_loss_scratch_bytes(n, H, W) bytes, 256-aligned.
+size_t image_loss_scratch_bytes(int n, int H, int W);
+cudaError_t launch_image_loss(const float* x, const float* y, int n, int H, int W,
+                              float w_ssim, float* grad, double* acc, float* loss_out,
+                              char* scratch, cudaStream_t s);
 // Exclusive prefix sum of 64-bit integers; *total receives the sum.
 cudaError_t launch_scan_u64(const unsigned long long* in, unsigned long long* out, int64_t n,
                             unsigned long long* part, unsigned long long* total,

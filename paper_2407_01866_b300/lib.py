@@ -42,7 +42,8 @@ class Config(ctypes.Structure):
                 ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_float),
                 ("theta_min", ctypes.c_float), ("theta_max", ctypes.c_float),
                 ("t_min", ctypes.c_float), ("t_max", ctypes.c_float),
-                ("mu_min", ctypes.c_float), ("mu_max", ctypes.c_float)]
+                ("mu_min", ctypes.c_float), ("mu_max", ctypes.c_float),
+                ("ssim_weight", ctypes.c_float)]
 
 
 class Stats(ctypes.Structure):
@@ -101,6 +102,10 @@ _SIGNATURES = {
                            ctypes.c_int32, ctypes.POINTER(Config), _P, ctypes.c_size_t,
                            ctypes.c_int64, _P, _P], ctypes.c_int),
     "igs_adam_update": ([ctypes.POINTER(FitState), ctypes.POINTER(Config), _P], ctypes.c_int),
+    "igs_image_loss_workspace_size": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "igs_image_loss": ([_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float,
+                        _P, _P, _P, ctypes.c_size_t, _P], ctypes.c_int),
     "igs_placement_workspace_size": ([ctypes.c_int32, ctypes.c_int32,
                                       ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "igs_init_gaussians": ([_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
@@ -249,6 +254,19 @@ def fit_step_half(state, params_half, target, H, W, cfg, ws, m_capacity, loss_ou
     _check(load().igs_fit_step_half(ctypes.byref(state), _ptr(params_half), dt, _ptr(target),
                                     H, W, ctypes.byref(cfg), _ptr(ws), ws.numel(), m_capacity,
                                     _ptr(loss_out), _stream(stream)))
+
+
+def image_loss(render, target, ssim_weight, grad_img, loss_out=None, ws=None, stream=None):
+    """L1 + ssim_weight * (1 - SSIM) of render against target ([n, H, W] each) and
+    its image-space gradient (Sec. 4.1)."""
+    n, H, W = target.shape
+    if ws is None:
+        b = ctypes.c_size_t()
+        _check(load().igs_image_loss_workspace_size(n, H, W, ctypes.byref(b)))
+        ws = alloc_workspace(b.value, target.device)
+    _check(load().igs_image_loss(_ptr(render), _ptr(target), n, H, W, ssim_weight,
+                                 _ptr(grad_img), _ptr(loss_out), _ptr(ws), ws.numel(),
+                                 _stream(stream)))
 
 
 def placement_workspace_size(H, W):

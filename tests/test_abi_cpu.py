@@ -104,3 +104,14 @@ def test_entry_points_reject_bad_arguments_without_a_gpu(lib):
     assert lib.igs_fit_step_half(ctypes.byref(st), ctypes.c_void_p(24576 + 2), 1,
                                  ctypes.c_void_p(28672), 16, 16, ctypes.byref(c), None, 0, 1,
                                  None, None) == L.IGS_ERR_ALIGN
+    assert lib.igs_image_loss(None, None, 0, 8, 8, ctypes.c_float(0.1), None, None, None, 0,
+                              None) == L.IGS_ERR_INVALID_ARG
+    assert lib.igs_image_loss(ctypes.c_void_p(4096), ctypes.c_void_p(8192), 3, 8, 8,
+                              ctypes.c_float(0.1), ctypes.c_void_p(12288), None,
+                              ctypes.c_void_p(16384 + 64), 1 << 20, None) == L.IGS_ERR_ALIGN
+    bad = L.default_config(ssim_weight=-1.0)
+    b = ctypes.c_size_t()
+    assert lib.igs_workspace_size(10, 3, 16, 16, ctypes.byref(bad), 100, ctypes.byref(b)) == \
+        L.IGS_ERR_INVALID_ARG
+    on = L.default_config(ssim_weight=0.1)
+    assert L.workspace_size(10, 3, 64, 64, on, 100) > L.workspace_size(10, 3, 64, 64, c, 100)
