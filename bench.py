@@ -44,6 +44,8 @@ FUSED_TRAFFIC_2048_RGB = 66.40e6
 # preprocess, 2 wide-Gaussian passes, 3 scan passes, emit, 2 segment sorts,
 # ranges, tile evaluations, fused adjoint, Adam
 KERNELS_PER_FIT_STEP = 14
+# the SSIM term adds the forward render and 4 image-loss passes
+SSIM_EXTRA_KERNELS = 5
 
 
 def fused_kernel_ops(evals, pixels, K, n):
@@ -208,7 +210,7 @@ def run_ours(args, w=WORKLOAD):
     dev = torch.device("cuda", local)
     H, W, n, N = w["H"], w["W"], w["n"], w["N"]
     target_np, P_np = make_inputs(rank_workload(w, rank))
-    cfg = L.default_config()
+    cfg = L.default_config(ssim_weight=args.ssim)
     target = torch.from_numpy(target_np).to(dev)
     P0 = torch.from_numpy(P_np).to(dev)
 
@@ -337,14 +339,16 @@ def run_ours(args, w=WORKLOAD):
             "dtype": "f32" if half is None else f"f32 math, {args.storage} parameter storage",
             "data": "synthetic",
             "config": {"workload": w["name"], "H": H, "W": W, "n": n, "N": N, "K": cfg.K,
-                       "storage": args.storage,
+                       "storage": args.storage, "loss": ("L1" if args.ssim == 0 else
+                                                         f"L1 + {args.ssim} SSIM"),
                        "bits_per_pixel": N * (5 + n) * (32 if half is None else 16) / (H * W),
                        "tile": cfg.tile, "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"independent fits x{world}"},
             "gaussian_pixel_evals_per_step": evals,
             "gaussian_pixel_evals_per_s": world * evals * 1000.0 / ms,
             "final_loss": float(loss.item()),
-            "gpu_launches": (KERNELS_PER_FIT_STEP + (0 if half is None else 2)) * args.steps,
+            "gpu_launches": (KERNELS_PER_FIT_STEP + (0 if half is None else 2)
+                             + (SSIM_EXTRA_KERNELS if args.ssim > 0 else 0)) * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
                          "unit": "T fp32 lane-ops/s", "frac": achieved / peak,
                          "traffic": (FUSED_TRAFFIC_2048_RGB
@@ -536,6 +540,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--workload", default="fit2048_rgb",
                     choices=list(FIT_WORKLOADS) + ["batch64", "decode8192"])
+    ap.add_argument("--ssim", type=float, default=0.0,
+                    help="weight of the SSIM term of the fit loss (Sec. 4.1 uses 0.1; "
+                         "0 = L1 with the fused adjoint)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="parameter storage of the fit workloads (f16/bf16: half copy "
                          "rendered, float32 master updated)")
