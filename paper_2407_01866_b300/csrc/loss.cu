@@ -4,8 +4,9 @@
 //
 // SSIM is computed per channel with an 11 x 11 Gaussian window (sigma 1.5,
 // normalised, zero-padded "same" correlation) and C1 = 0.01^2, C2 = 0.03^2;
-// L_SSIM = 1 - mean SSIM over channels and pixels. Four passes, one thread
-// per (channel, pixel), float32:
+// L_SSIM = 1 - mean SSIM over channels and pixels. Four passes, float32;
+// the horizontal ones take one thread per (channel, pixel), the vertical ones
+// one thread per (channel, column, strip of RS rows):
 //   h5  horizontal window sums of x, y, x^2, y^2, x y
 //   v5  vertical sums -> mu_x, mu_y, E[x^2], E[y^2], E[xy] -> SSIM and its
 //       partials G1 = dS/dmu_x, G2 = dS/dE[x^2], G3 = dS/dE[xy]; the loss sum
@@ -56,37 +57,62 @@ __global__ void __launch_bounds__(256) k_h5(const float* x, const float* y, int6
   }
 }
 
+// Vertical passes: a thread covers RS consecutive rows of one column and
+// slides down them, so every loaded row feeds up to 2 WR + 1 outputs.
+constexpr int RS = 8;
+
 __global__ void __launch_bounds__(256) k_v5(const float* hm, const float* x, const float* y,
-                                            int64_t total, int H, int W, Win w, float w_ssim,
-                                            float* G, double* acc) {
+                                            int64_t total, int n, int H, int W, Win w,
+                                            float w_ssim, float* G, double* acc) {
   const int64_t HW = (int64_t)H * W;
+  const int strips = (H + RS - 1) / RS;
+  const int64_t items = (int64_t)n * strips * W;
   double part = 0.0;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int yy = (int)((p % HW) / W);
-    float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const int xx = (int)(it % W);
+    const int64_t cs = it / W;
+    const int y0 = (int)(cs % strips) * RS;
+    const int64_t cbase = (cs / strips) * HW;
+    float m[5][RS];
 #pragma unroll
-    for (int i = -WR; i <= WR; ++i) {
-      const int ys = yy + i;
-      if (ys < 0 || ys >= H) continue;
-      const int64_t o = p + (int64_t)i * W;
-      const float g = w.g[i + WR];
+    for (int k = 0; k < 5; ++k)
 #pragma unroll
-      for (int k = 0; k < 5; ++k) m[k] = fmaf(g, hm[k * total + o], m[k]);
+      for (int j = 0; j < RS; ++j) m[k][j] = 0.0f;
+#pragma unroll
+    for (int rr = 0; rr < RS + 2 * WR; ++rr) {
+      const int r = y0 - WR + rr;
+      if (r < 0 || r >= H) continue;
+      const int64_t o = cbase + (int64_t)r * W + xx;
+      float v[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) v[k] = hm[k * total + o];
+#pragma unroll
+      for (int j = 0; j < RS; ++j) {
+        const int i = rr - WR - j;  // tap offset of row r for output row y0 + j
+        if (i < -WR || i > WR) continue;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) m[k][j] = fmaf(w.g[i + WR], v[k], m[k][j]);
+      }
     }
-    const float mx = m[0], my = m[1];
-    const float vx = m[2] - mx * mx, vy = m[3] - my * my, cxy = m[4] - mx * my;
-    const float A1 = 2.f * mx * my + C1, A2 = 2.f * cxy + C2;
-    const float B1 = mx * mx + my * my + C1, B2 = vx + vy + C2;
-    const float iB = 1.f / (B1 * B2);
-    const float S = A1 * A2 * iB;
-    const float dS_dvx = -S / B2;
-    const float dS_dcxy = 2.f * A1 * iB;
-    const float dmx = 2.f * my * A2 * iB - S * 2.f * mx / B1;
-    G[p] = dmx - 2.f * mx * dS_dvx - my * dS_dcxy;
-    G[total + p] = dS_dvx;
-    G[2 * total + p] = dS_dcxy;
-    part += (double)fabsf(x[p] - y[p]) + (double)w_ssim * (1.0 - (double)S);
+#pragma unroll
+    for (int j = 0; j < RS; ++j) {
+      if (y0 + j >= H) break;
+      const int64_t p = cbase + (int64_t)(y0 + j) * W + xx;
+      const float mx = m[0][j], my = m[1][j];
+      const float vx = m[2][j] - mx * mx, vy = m[3][j] - my * my, cxy = m[4][j] - mx * my;
+      const float A1 = 2.f * mx * my + C1, A2 = 2.f * cxy + C2;
+      const float B1 = mx * mx + my * my + C1, B2 = vx + vy + C2;
+      const float iB = 1.f / (B1 * B2);
+      const float S = A1 * A2 * iB;
+      const float dS_dvx = -S / B2;
+      const float dS_dcxy = 2.f * A1 * iB;
+      const float dmx = 2.f * my * A2 * iB - S * 2.f * mx / B1;
+      G[p] = dmx - 2.f * mx * dS_dvx - my * dS_dcxy;
+      G[total + p] = dS_dvx;
+      G[2 * total + p] = dS_dcxy;
+      part += (double)fabsf(x[p] - y[p]) + (double)w_ssim * (1.0 - (double)S);
+    }
   }
   part = warp_sum<double>(part);
   if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(acc, part);
@@ -114,26 +140,47 @@ __global__ void __launch_bounds__(256) k_h3(const float* G, int64_t total, int H
 }
 
 __global__ void __launch_bounds__(256) k_v3(const float* hg, const float* x, const float* y,
-                                            int64_t total, int H, int W, Win w, float w_ssim,
-                                            float inv_m, float* grad) {
+                                            int64_t total, int n, int H, int W, Win w,
+                                            float w_ssim, float inv_m, float* grad) {
   const int64_t HW = (int64_t)H * W;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int yy = (int)((p % HW) / W);
-    float b[3] = {0.f, 0.f, 0.f};
+  const int strips = (H + RS - 1) / RS;
+  const int64_t items = (int64_t)n * strips * W;
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < items;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const int xx = (int)(it % W);
+    const int64_t cs = it / W;
+    const int y0 = (int)(cs % strips) * RS;
+    const int64_t cbase = (cs / strips) * HW;
+    float b[3][RS];
 #pragma unroll
-    for (int i = -WR; i <= WR; ++i) {
-      const int ys = yy + i;
-      if (ys < 0 || ys >= H) continue;
-      const int64_t o = p + (int64_t)i * W;
-      const float g = w.g[i + WR];
+    for (int k = 0; k < 3; ++k)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) b[k] = fmaf(g, hg[k * total + o], b[k]);
+      for (int j = 0; j < RS; ++j) b[k][j] = 0.0f;
+#pragma unroll
+    for (int rr = 0; rr < RS + 2 * WR; ++rr) {
+      const int r = y0 - WR + rr;
+      if (r < 0 || r >= H) continue;
+      const int64_t o = cbase + (int64_t)r * W + xx;
+      float v[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) v[k] = hg[k * total + o];
+#pragma unroll
+      for (int j = 0; j < RS; ++j) {
+        const int i = rr - WR - j;
+        if (i < -WR || i > WR) continue;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) b[k][j] = fmaf(w.g[i + WR], v[k], b[k][j]);
+      }
     }
-    const float xv = x[p], yv = y[p];
-    const float d = xv - yv;
-    const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-    grad[p] = sgn * inv_m - w_ssim * inv_m * (b[0] + 2.f * xv * b[1] + yv * b[2]);
+#pragma unroll
+    for (int j = 0; j < RS; ++j) {
+      if (y0 + j >= H) break;
+      const int64_t p = cbase + (int64_t)(y0 + j) * W + xx;
+      const float xv = x[p], yv = y[p];
+      const float d = xv - yv;
+      const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+      grad[p] = sgn * inv_m - w_ssim * inv_m * (b[0][j] + 2.f * xv * b[1][j] + yv * b[2][j]);
+    }
   }
 }
 
@@ -193,9 +240,10 @@ cudaError_t launch_image_loss(const float* x, const float* y, int n, int H, int 
     float* hm = reinterpret_cast<float*>(scratch + 256);  // [5][total], then [3][total]
     float* G = hm + 5 * total;                             // [3][total]
     k_h5<<<grid_for(total), 256, 0, s>>>(x, y, total, H, W, w, hm);
-    k_v5<<<grid_for(total), 256, 0, s>>>(hm, x, y, total, H, W, w, w_ssim, G, acc);
+    const int64_t strips = (int64_t)n * ((H + RS - 1) / RS) * W;
+    k_v5<<<grid_for(strips), 256, 0, s>>>(hm, x, y, total, n, H, W, w, w_ssim, G, acc);
     k_h3<<<grid_for(total), 256, 0, s>>>(G, total, H, W, w, hm);
-    k_v3<<<grid_for(total), 256, 0, s>>>(hm, x, y, total, H, W, w, w_ssim, inv_m, grad);
+    k_v3<<<grid_for(strips), 256, 0, s>>>(hm, x, y, total, n, H, W, w, w_ssim, inv_m, grad);
   }
   if (loss_out) k_loss_out<<<1, 32, 0, s>>>(acc, inv_m, loss_out);
   return cudaGetLastError();
