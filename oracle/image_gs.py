@@ -23,7 +23,7 @@ What it computes (Image-GS, Sec. 3.1-3.3 and Sec. 4.1):
   clipping theta and the scales to valid ranges after each update (Sec. 3.1).
   Gradients pass through the K retained Gaussians only (Sec. 3.3).
 
-Readings where the paper is silent (all listed in the design doc): pixel (h, w) is
+Readings where the paper is silent (the same as the library header's): pixel (h, w) is
 evaluated at its centre (w + 1/2, h + 1/2) in pixels, x along the width, y
 down the rows; mu in pixels is mu_px = (fl32(mu_x * W), fl32(mu_y * H)) -- the
 binary32 product is the input's rounding point; tile j is the closed rectangle

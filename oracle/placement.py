@@ -14,7 +14,7 @@ What it computes:
   |c_r(x) - c_t(x)| / sum |c_r - c_t|, and a Gaussian is initialised there
   the same way.
 
-Readings where the paper is silent (listed in the design doc):
+Readings where the paper is silent (the same as the library header's):
 
 * grad I: per channel, central differences (I[x+1] - I[x-1]) / 2 inside the
   image and one-sided differences at the borders (zero along an axis of

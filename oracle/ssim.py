@@ -5,7 +5,7 @@ CPU arms of `bench.py` may import this module. It shares no code with the
 CUDA path.
 
 Sec. 4.1 fits against L1 + 0.1 * L_SSIM. The paper does not define L_SSIM
-further; the readings here (listed in the design doc) are the standard structural
+further; the readings here (the same as the library header's) are the standard structural
 similarity of Wang et al.:
 
 * per channel, local statistics under an 11 x 11 Gaussian window with
