@@ -5,8 +5,8 @@
 // SSIM is computed per channel with an 11 x 11 Gaussian window (sigma 1.5,
 // normalised, zero-padded "same" correlation) and C1 = 0.01^2, C2 = 0.03^2;
 // L_SSIM = 1 - mean SSIM over channels and pixels. Four passes, float32;
-// the horizontal ones take one thread per (channel, pixel), the vertical ones
-// one thread per (channel, column, strip of RS rows):
+// the horizontal ones stage row segments in shared memory, the vertical ones
+// take one thread per (channel, column, strip of RS rows):
 //   h5  horizontal window sums of x, y, x^2, y^2, x y
 //   v5  vertical sums -> mu_x, mu_y, E[x^2], E[y^2], E[xy] -> SSIM and its
 //       partials G1 = dS/dmu_x, G2 = dS/dE[x^2], G3 = dS/dE[xy]; the loss sum
@@ -29,26 +29,38 @@ struct Win {
   float g[2 * WR + 1];
 };
 
-__global__ void __launch_bounds__(256) k_h5(const float* x, const float* y, int64_t total,
-                                            int H, int W, Win w, float* out) {
-  const int64_t HW = (int64_t)H * W;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t q = p % HW;
-    const int xx = (int)(q % W);
-    const int64_t row = p - xx;
+// Horizontal passes: a CTA takes a row segment of HSEG outputs, stages it
+// with its halo in shared memory once, and every thread sums its taps there.
+constexpr int HSEG = 256;
+
+__global__ void __launch_bounds__(HSEG) k_h5(const float* x, const float* y, int64_t rows,
+                                             int W, Win w, int64_t total, float* out) {
+  __shared__ float sx[HSEG + 2 * WR], sy[HSEG + 2 * WR];
+  const int segs = (W + HSEG - 1) / HSEG;
+  for (int64_t b = blockIdx.x; b < rows * segs; b += gridDim.x) {
+    const int64_t row = (b / segs) * W;  // start of the (channel, row) in the planes
+    const int x0 = (int)(b % segs) * HSEG;
+    __syncthreads();
+    for (int k = threadIdx.x; k < HSEG + 2 * WR; k += blockDim.x) {
+      const int xs = x0 - WR + k;
+      const bool in = xs >= 0 && xs < W;
+      sx[k] = in ? x[row + xs] : 0.0f;
+      sy[k] = in ? y[row + xs] : 0.0f;
+    }
+    __syncthreads();
+    const int xx = x0 + threadIdx.x;
+    if (xx >= W) continue;
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
 #pragma unroll
-    for (int i = -WR; i <= WR; ++i) {
-      const int xs = xx + i;
-      if (xs < 0 || xs >= W) continue;
-      const float a = x[row + xs], b = y[row + xs], g = w.g[i + WR];
+    for (int i = 0; i <= 2 * WR; ++i) {
+      const float a = sx[threadIdx.x + i], c = sy[threadIdx.x + i], g = w.g[i];
       s0 = fmaf(g, a, s0);
-      s1 = fmaf(g, b, s1);
+      s1 = fmaf(g, c, s1);
       s2 = fmaf(g, a * a, s2);
-      s3 = fmaf(g, b * b, s3);
-      s4 = fmaf(g, a * b, s4);
+      s3 = fmaf(g, c * c, s3);
+      s4 = fmaf(g, a * c, s4);
     }
+    const int64_t p = row + xx;
     out[p] = s0;
     out[total + p] = s1;
     out[2 * total + p] = s2;
@@ -118,24 +130,31 @@ __global__ void __launch_bounds__(256) k_v5(const float* hm, const float* x, con
   if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(acc, part);
 }
 
-__global__ void __launch_bounds__(256) k_h3(const float* G, int64_t total, int H, int W, Win w,
-                                            float* out) {
-  const int64_t HW = (int64_t)H * W;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int xx = (int)((p % HW) % W);
-    const int64_t row = p - xx;
-    float s[3] = {0.f, 0.f, 0.f};
+__global__ void __launch_bounds__(HSEG) k_h3(const float* G, int64_t rows, int W, Win w,
+                                             int64_t total, float* out) {
+  __shared__ float sg[3][HSEG + 2 * WR];
+  const int segs = (W + HSEG - 1) / HSEG;
+  for (int64_t b = blockIdx.x; b < rows * segs; b += gridDim.x) {
+    const int64_t row = (b / segs) * W;
+    const int x0 = (int)(b % segs) * HSEG;
+    __syncthreads();
+    for (int k = threadIdx.x; k < HSEG + 2 * WR; k += blockDim.x) {
+      const int xs = x0 - WR + k;
+      const bool in = xs >= 0 && xs < W;
 #pragma unroll
-    for (int i = -WR; i <= WR; ++i) {
-      const int xs = xx + i;
-      if (xs < 0 || xs >= W) continue;
-      const float g = w.g[i + WR];
+      for (int m = 0; m < 3; ++m) sg[m][k] = in ? G[m * total + row + xs] : 0.0f;
+    }
+    __syncthreads();
+    const int xx = x0 + threadIdx.x;
+    if (xx >= W) continue;
+    float acc[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-      for (int k = 0; k < 3; ++k) s[k] = fmaf(g, G[k * total + row + xs], s[k]);
+    for (int i = 0; i <= 2 * WR; ++i) {
+#pragma unroll
+      for (int m = 0; m < 3; ++m) acc[m] = fmaf(w.g[i], sg[m][threadIdx.x + i], acc[m]);
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) out[k * total + p] = s[k];
+    for (int m = 0; m < 3; ++m) out[m * total + row + xx] = acc[m];
   }
 }
 
@@ -239,10 +258,13 @@ cudaError_t launch_image_loss(const float* x, const float* y, int n, int H, int 
     const Win w = window();
     float* hm = reinterpret_cast<float*>(scratch + 256);  // [5][total], then [3][total]
     float* G = hm + 5 * total;                             // [3][total]
-    k_h5<<<grid_for(total), 256, 0, s>>>(x, y, total, H, W, w, hm);
+    const int64_t rows = (int64_t)n * H;
+    const int64_t segs = rows * ((W + HSEG - 1) / HSEG);
+    const unsigned hgrid = (unsigned)(segs < 148 * 16 ? segs : 148 * 16);
+    k_h5<<<hgrid, HSEG, 0, s>>>(x, y, rows, W, w, total, hm);
     const int64_t strips = (int64_t)n * ((H + RS - 1) / RS) * W;
     k_v5<<<grid_for(strips), 256, 0, s>>>(hm, x, y, total, n, H, W, w, w_ssim, G, acc);
-    k_h3<<<grid_for(total), 256, 0, s>>>(G, total, H, W, w, hm);
+    k_h3<<<hgrid, HSEG, 0, s>>>(G, rows, W, w, total, hm);
     k_v3<<<grid_for(strips), 256, 0, s>>>(hm, x, y, total, n, H, W, w, w_ssim, inv_m, grad);
   }
   if (loss_out) k_loss_out<<<1, 32, 0, s>>>(acc, inv_m, loss_out);
