@@ -130,3 +130,29 @@ def test_autotune_and_graph_replay():
     assert int(st.step.item()) == 41
     last = loss.cpu().numpy()
     assert (last < first).all(), (first, last)
+
+
+@pytest.mark.parametrize("K,normalize", [(3, 1), (0, 0), (16, 1)])
+def test_batched_step_equals_single_image_steps_in_other_modes(K, normalize):
+    Hs, Ws, Ns, Ps, Ts = make_batch(seed=9)
+    cfg = L.default_config(K=K, normalize=normalize)
+    shape = L.batch_shape(Hs, Ws, Ns, 3)
+    cap = 16 * sum(Ns) + 1024
+    ws = L.alloc_workspace(L.batch_workspace_size(shape, cfg, cap))
+    L.batch_setup(shape, cfg, ws, cap)
+    st = State(np.concatenate(Ps))
+    tg = dev(np.concatenate([t.ravel() for t in Ts]))
+    loss = torch.zeros(len(Hs), device="cuda")
+    L.fit_batch_step(st.c, tg, shape, cfg, ws, cap, loss_out=loss)
+    torch.cuda.synchronize()
+    gb = split(st.G.cpu().numpy().astype(np.float64), Ns)
+    lb = loss.cpu().numpy()
+    for b in range(len(Hs)):
+        s1 = State(Ps[b])
+        w1 = L.alloc_workspace(L.workspace_size(Ns[b], 3, Hs[b], Ws[b], cfg, 16 * Ns[b] + 64))
+        l1 = torch.zeros(1, device="cuda")
+        L.fit_step(s1.c, dev(Ts[b]), Hs[b], Ws[b], cfg, w1, 16 * Ns[b] + 64, l1)
+        torch.cuda.synchronize()
+        assert abs(l1.item() - lb[b]) <= 1e-6 * max(1.0, abs(lb[b])), b
+        errs = grad_rel_error(gb[b], s1.G.cpu().numpy().astype(np.float64))
+        assert max(errs.values()) <= 1e-4, (b, errs)
