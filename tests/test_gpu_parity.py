@@ -270,3 +270,22 @@ def test_equal_keys_at_the_kth_place_go_to_smaller_indices(case):
     cen = O.pixel_centres(pix)
     dec = gs.decode(cen.astype(np.float32))
     assert np.abs(dec - O.render_points(g, cen, H, W, K=K, tile=tile)).max() <= PIX_TOL
+
+
+def test_autograd_render_matches_oracle_forward_and_adjoint():
+    """lib.render is a torch.autograd.Function over the C ABI: its output is
+    the forward render and its backward the adjoint of the upstream gradient."""
+    H, W, N, n = 48, 40, 250, 3
+    g = oset(N, n, 21)
+    ts = [torch.from_numpy(a.copy()).cuda().requires_grad_(True)
+          for a in (g.xy, g.theta, g.inv_scale, g.color)]
+    img = L.render(*ts, H, W)
+    np.testing.assert_allclose(img.detach().cpu().numpy(), O.render_image(g, H, W),
+                               rtol=0, atol=PIX_TOL)
+    weight = np.random.default_rng(22).standard_normal((n, H, W)).astype(np.float32)
+    (img * torch.from_numpy(weight).cuda()).sum().backward()
+    got = np.concatenate([ts[0].grad.cpu().numpy(), ts[1].grad.cpu().numpy()[:, None],
+                          ts[2].grad.cpu().numpy(), ts[3].grad.cpu().numpy()], axis=1)
+    want = O.backward_image(g, weight, H, W)
+    errs = grad_rel_error(got.astype(np.float64), want)
+    assert max(errs.values()) <= GRAD_TOL, errs
