@@ -1074,13 +1074,27 @@ __global__ void __launch_bounds__(256) k_decode(RenderParams p) {
       tq[k] = F_INF;
       tp[k] = -1;
     }
-    for (int j = range.x; j < range.y; ++j) {
-      const int id = p.list[j];
-      if ((unsigned)id >= (unsigned)p.N) continue;
-      const GRec g = p.rec[id];
-      const float q = rank_key(px, py, g.a.x, g.a.y, g.a.z, g.a.w, g.b.x);
-      if (q < tq[KS<K>::A - 1] || (q == tq[KS<K>::A - 1] && id < tp[KS<K>::A - 1]))
-        topk_insert<KS<K>::A>(tq, tp, q, id);
+    // four candidates per round: their index and record loads are in flight
+    // together (the walk is bound by dependent L2 latencies)
+    for (int j0 = range.x; j0 < range.y; j0 += 4) {
+      int id[4];
+      float q[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) id[u] = j0 + u < range.y ? p.list[j0 + u] : -1;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool ok = (unsigned)id[u] < (unsigned)p.N;
+        const float4 a = ok ? p.rec[id[u]].a : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float a11 = ok ? p.rec[id[u]].b.x : 0.0f;
+        q[u] = ok ? rank_key(px, py, a.x, a.y, a.z, a.w, a11) : F_INF;
+        if (!ok) id[u] = -1;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (id[u] < 0) continue;
+        if (q[u] < tq[KS<K>::A - 1] || (q[u] == tq[KS<K>::A - 1] && id[u] < tp[KS<K>::A - 1]))
+          topk_insert<KS<K>::A>(tq, tp, q[u], id[u]);
+      }
     }
     const float q0 = p.normalize ? tq[0] : 0.0f;
 #pragma unroll
