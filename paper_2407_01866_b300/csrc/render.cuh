@@ -239,6 +239,7 @@ struct PixelBlend {
   float tau;        // K-th key (+inf if |S_j| < K)
   float q0;         // smallest key (0 when unnormalised)
   int gcut;         // largest index admitted among winners whose key equals tau
+  int nw;           // winners recorded by pass B for pass C (fast path adjoint)
 };
 
 // ---------------------------------------------------------------------------
@@ -408,19 +409,27 @@ __device__ __forceinline__ int tie_cutoff(int cnt, float px, float py, bool tie,
   return tie ? gc : GID_NONE;
 }
 
-// Pass B over the staged list: membership, blend, and (MASKS) the ballot of
-// winning live pixels of this warp per candidate into mask_w[].
-template <int K, int NC, int CH, bool MASKS>
+// Pass B over the staged list: membership and blend. With REC (the fast
+// adjoint) it also records, for pass C, the winners of every live pixel: the
+// pixel's k-th winner goes to wrec[k * NT] as (staged index << 5 | rank of the
+// pixel among this warp's winning live pixels of that candidate), and the
+// number of such pixels of this warp goes to cnt_w[j] for every staged j.
+// A pixel has at most K winners (pass A's culling never drops a key <= tau),
+// so at most A records; the guard only keeps the stores in bounds.
+template <int K, int NC, int CH, int NT, bool REC>
 __device__ __forceinline__ void culled_blend(const RenderParams& p, int cnt, float px, float py,
                                              bool live, const float4& R,
                                              const float (&tq)[KS<K>::A], float mdrop,
                                              const float4* s_a, const float2* s_b,
                                              const float2* s_e, const float* s_col,
-                                             unsigned* mask_w, PixelBlend<Chan<NC>::R>& r) {
+                                             unsigned* cnt_w, unsigned short* wrec,
+                                             PixelBlend<Chan<NC>::R>& r) {
   constexpr int NCR = Chan<NC>::R;
   constexpr int A = KS<K>::A;
   const int n = nchan<NC>(p);
   const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;  // lanes below this one
+  r.nw = 0;
   r.q0 = p.normalize ? tq[0] : 0.0f;
   r.tau = K == 0 ? F_INF : tq[A - 1];
   r.gcut = GID_NONE;
@@ -437,13 +446,18 @@ __device__ __forceinline__ void culled_blend(const RenderParams& p, int cnt, flo
     const int jl = c0 + lane;
     const bool in = jl < cnt;
     const bool surv = in && !(key_lower_bound(s_a[jl], s_b[jl].x, s_e[jl], R) > T);
-    if (MASKS && in && !surv) mask_w[jl] = 0u;
+    if (REC && in && !surv) cnt_w[jl] = 0u;
     unsigned m = __ballot_sync(FULL_MASK, surv);
     auto take = [&](int j, float q, int gid) {
       const bool win = q < r.tau || (q == r.tau && gid <= r.gcut);
-      if (MASKS) {
-        const unsigned bal = __ballot_sync(FULL_MASK, win && live);
-        if (lane == 0) mask_w[j] = bal;
+      if (REC) {
+        const bool rec = win && live && r.nw < A;
+        const unsigned bal = __ballot_sync(FULL_MASK, rec);
+        if (lane == 0) cnt_w[j] = __popc(bal);
+        if (rec) {
+          wrec[r.nw * NT] = (unsigned short)((j << 5) | __popc(bal & lt));
+          ++r.nw;
+        }
       }
       if (win) {
         const float w = blend_weight(r.q0, q);  // exactly 1 at q = q_min
@@ -498,8 +512,8 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(RenderParams p) {
     const float4 R = block_rect<TILE>(x0, y0);
     float mdrop;
     culled_keys<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tq, mdrop);
-    culled_blend<K, NC, NT, false>(p, len, px, py, in_img, R, tq, mdrop, s_a, s_b, s_e, s_col,
-                                   nullptr, r);
+    culled_blend<K, NC, NT, NT, false>(p, len, px, py, in_img, R, tq, mdrop, s_a, s_b, s_e,
+                                       s_col, nullptr, nullptr, r);
   } else {
     select_keys<TILE, K, NT>(p, range, px, py, tq, s_a, s_b);
     blend_pass<TILE, K, NC, NT>(p, range, px, py, tq, r, s_a, s_b, s_col);
@@ -539,10 +553,14 @@ __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   L.col = o;    o = al4(o + n * CH);      // staged colours, channel-major
   L.ps0 = o;    o += 4 * NT;              // float4 (px, py, q0, beta) per pixel
   L.gh = o;     o = al4(o + n * NT);      // per-pixel -g/(2Z), channel-major
-  L.slot_a = o; o = al4(o + np * CH);     // pass C per-candidate sums; (ex, ey) before
-  L.slot_b = o; o = al4(o + np * NT);     // pass C per-thread sums; rank keys before
-  // ballots, then pass C's 16-bit pair table (<= 16 NT pairs); chunked (tau, cut-off)
-  L.mask = o;   o += (NWB * CH > 8 * NT ? NWB * CH : 8 * NT);
+  // pass C per-candidate sums A_j; before them (ex, ey) of the staged
+  // candidates, followed by pass B's NWB x CH counts (2 + NWB <= 10 <= 2 np
+  // words per candidate, as np >= 6 and CH <= NT, so they end inside slot_b)
+  L.slot_a = o; o = al4(o + np * CH);
+  L.slot_b = o; o = al4(o + np * NT);     // pass C per-thread sums B_t; rank keys before
+  // pass B's 16-bit winner records, then pass C's pair table (<= 16 NT
+  // entries each); the chunked path's (tau, cut-off) per pixel
+  L.mask = o;   o += 8 * NT;
   L.coff = o;   o += CH + 1;              // first pair of every candidate
   L.loss = (o + 1) & ~1; o = L.loss + 2 * NWB + 2;  // doubles
   L.scan = o;   o += 34;                  // integer block-scan scratch
@@ -621,58 +639,60 @@ __device__ __forceinline__ int div_small(int a, int d, float inv) {
 
 // Pass C of the fast path. The winning (candidate, pixel) pairs, in
 // (candidate, warp block, pixel) order, are first written out as a table of
-// 16-bit entries (candidate << 8 | pixel) over the ballot masks' storage (each
-// thread reads its masks into registers before the offset scan's barriers).
-// The table is split into equal contiguous ranges, one per thread; a thread
+// 16-bit entries (candidate << 8 | pixel) by a counting sort of pass B's
+// records: a scan over candidates of their per-warp-block counts gives every
+// (candidate, warp block) its first slot, and each pixel stores its own
+// winners at that slot plus its rank (the records are read into registers
+// before the scan's barriers, as the table overwrites them). The table is split into equal contiguous ranges, one per thread; a thread
 // accumulates the candidates of its range in registers. A candidate's partial
 // sums go to the candidate's slot A_j, written by the one thread whose range
 // holds the candidate's first pair, or, for the candidate a range opens with
 // when it began in an earlier range, to that thread's slot B_t. After a
 // barrier, the thread of candidate j adds A_j and the B_t of the later
 // threads its pairs reach, and turns the sums into parameter gradients.
-// Needs at most NT * 16 pairs (K <= 16).
-template <int TILE, int NC, int CH>
+// Needs at most NT * 16 pairs (K <= 16): s_win / s_pair hold 16 NT entries.
+template <int TILE, int K, int NC, int CH>
 __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx& t, int cnt,
-                                            const float4* s_a, const float2* s_b,
-                                            const float* s_col, unsigned* s_mask,
-                                            const float4* s_ps0, const float* s_gh,
-                                            float* s_slot_a, float* s_slot_b, int* s_coff,
-                                            int* s_scan) {
+                                            int nw, const float4* s_a, const float2* s_b,
+                                            const float* s_col, unsigned short* s_win,
+                                            unsigned* s_cnt, const float4* s_ps0,
+                                            const float* s_gh, float* s_slot_a, float* s_slot_b,
+                                            int* s_coff, int* s_scan) {
   constexpr int NT = TILE * TILE;
   constexpr int NWB = NT / 32;
   constexpr int NCR = Chan<NC>::R;
-  constexpr int MAXIT = (NWB * CH + NT - 1) / NT;  // items per thread in the scan
+  constexpr int A = KS<K>::A;
   const int n = nchan<NC>(p);
-  const int nit = cnt * NWB;
-  // item it = (candidate it / NWB, warp block it % NWB); per_it consecutive
-  // items per thread
-  const int per_it = (nit + NT - 1) / NT;
-  const int i0 = (int)threadIdx.x * per_it;
-  unsigned mk[MAXIT];
-  int loc = 0;
+  const int tid = threadIdx.x;
+  // this pixel's records, and candidate tid's counts per warp block
+  unsigned short ew[A];
 #pragma unroll
-  for (int k = 0; k < MAXIT; ++k) {
-    const int it = i0 + k;
-    mk[k] = (k < per_it && it < nit) ? s_mask[(it % NWB) * CH + it / NWB] : 0u;
-    loc += __popc(mk[k]);
+  for (int k = 0; k < A; ++k) ew[k] = k < nw ? s_win[k * NT + tid] : (unsigned short)0;
+  int pre[NWB];
+  int tot = 0;
+#pragma unroll
+  for (int wb = 0; wb < NWB; ++wb) {
+    pre[wb] = tot;
+    if (tid < cnt) tot += (int)s_cnt[wb * CH + tid];
   }
   int P;
-  int run = block_scan_int(loc, s_scan, P);  // its barriers end every read of s_mask
-  unsigned short* s_pair = reinterpret_cast<unsigned short*>(s_mask);
+  const int base = block_scan_int(tid < cnt ? tot : 0, s_scan, P);  // ends every read of s_win
+  if (tid < cnt) {
 #pragma unroll
-  for (int k = 0; k < MAXIT; ++k) {
-    const int it = i0 + k;
-    if (k < per_it && it < nit) {
-      const int j = it / NWB, wb = it % NWB;
-      if (wb == 0) s_coff[j] = run;
-      unsigned m = mk[k];
-      while (m) {
-        s_pair[run++] = (unsigned short)((j << 8) | (wb * 32 + __ffs(m) - 1));
-        m &= m - 1;
-      }
+    for (int wb = 0; wb < NWB; ++wb) s_cnt[wb * CH + tid] = (unsigned)(base + pre[wb]);
+    s_coff[tid] = base;
+  }
+  if (tid == 0) s_coff[cnt] = P;
+  __syncthreads();
+  unsigned short* s_pair = s_win;
+  const unsigned* s_first = s_cnt + (tid >> 5) * CH;  // first slot of (candidate, my warp block)
+#pragma unroll
+  for (int k = 0; k < A; ++k) {
+    if (k < nw) {
+      const int j = ew[k] >> 5;
+      s_pair[s_first[j] + (ew[k] & 31u)] = (unsigned short)((j << 8) | tid);
     }
   }
-  if (threadIdx.x == 0) s_coff[cnt] = P;
   const int per = (P + NT - 1) / NT;  // pairs per thread
   const float inv_per = per > 0 ? 1.0f / (float)per : 0.0f;
   __syncthreads();
@@ -883,8 +903,12 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   float* s_slot_b = smem + SL.slot_b;
   float2* s_e = reinterpret_cast<float2*>(s_slot_a);      // until pass C
   unsigned* s_key = reinterpret_cast<unsigned*>(s_slot_b);  // while staging
-  unsigned* s_mask = reinterpret_cast<unsigned*>(smem + SL.mask);
+  // pass B's per-pixel records, then pass C's pair table (fast path)
+  unsigned short* s_win = reinterpret_cast<unsigned short*>(smem + SL.mask);
   float2* s_ps1 = reinterpret_cast<float2*>(smem + SL.mask);  // chunked path only
+  // per (warp block, candidate) counts of pass B, then first pair slots; after
+  // (ex, ey), in pass C's sums' storage, which is free until its loop
+  unsigned* s_cnt = reinterpret_cast<unsigned*>(s_slot_a) + 2 * CH;
   double* s_loss = reinterpret_cast<double*>(smem + SL.loss);
 
   const int2 lp = pixel_of<TILE>(threadIdx.x);
@@ -914,8 +938,9 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
     const float4 R = block_rect<TILE>(t.x0, t.y0);
     float mdrop;
     culled_keys<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tq, mdrop);
-    culled_blend<K, NC, CH, (K > 0)>(p, len, px, py, in_img, R, tq, mdrop, s_a, s_b, s_e,
-                                     s_col, s_mask + (threadIdx.x >> 5) * CH, r);
+    culled_blend<K, NC, CH, NT, (K > 0)>(p, len, px, py, in_img, R, tq, mdrop, s_a, s_b, s_e,
+                                         s_col, s_cnt + (threadIdx.x >> 5) * CH,
+                                         s_win + threadIdx.x, r);
   } else {
     select_keys<TILE, K, CH>(p, t.range, px, py, tq, s_a, s_b);
     blend_pass<TILE, K, NC, CH>(p, t.range, px, py, tq, r, s_a, s_b, s_col);
@@ -962,9 +987,9 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
 
   // ---- pass C: candidate-major accumulation of the adjoint
   if (flat) {
-    flat_pass_c<TILE, NC, CH>(p, t, len, s_a, s_b, s_col, s_mask, s_ps0, s_gh, s_slot_a,
-                              s_slot_b, reinterpret_cast<int*>(smem + SL.coff),
-                              reinterpret_cast<int*>(smem + SL.scan));
+    flat_pass_c<TILE, K, NC, CH>(p, t, len, r.nw, s_a, s_b, s_col, s_win, s_cnt, s_ps0, s_gh,
+                                 s_slot_a, s_slot_b, reinterpret_cast<int*>(smem + SL.coff),
+                                 reinterpret_cast<int*>(smem + SL.scan));
   } else {
     chunked_pass_c<TILE, NC, CH>(p, t, s_ps0, s_ps1, s_gh, s_slot_a);
   }
