@@ -344,8 +344,29 @@ __device__ __forceinline__ void culled_keys(const RenderParams& p, int cnt, floa
   if (K == 0 && !p.normalize) return;
   const int lane = threadIdx.x & 31;
   float thr = F_INF;  // no lane of the block can use a key above this
-  // a first group of 16 gives every lane K keys early (nearest first)
-  for (int c0 = 0, gw = 16; c0 < cnt; c0 += gw, gw = 32) {
+  int c0 = 0, gw = 16;
+  if (K > 0) {
+    // the first A candidates (nearest first) fill the empty top K: the k-th
+    // insertion meets only slots 0..k, the later slots still holding +inf,
+    // and drops nothing (a NaN key from a corrupt entry inserts nothing)
+#pragma unroll
+    for (int k = 0; k < A; ++k) {
+      const float4 a = s_a[k];
+      const float q = k < cnt ? rank_key(px, py, a.x, a.y, a.z, a.w, s_b[k].x) : F_INF;
+      float x = q < F_INF ? q : F_INF;
+#pragma unroll
+      for (int s2 = 0; s2 <= k; ++s2) {
+        const float lo = fminf(tq[s2], x);
+        x = fmaxf(tq[s2], x);
+        tq[s2] = lo;
+      }
+    }
+    c0 = A;
+    gw = 32;
+    thr = warp_max_key(live ? tq[A - 1] : 0.0f);
+  }
+  // (K = 0: a first group of 16 then groups of 32)
+  for (; c0 < cnt; c0 += gw, gw = 32) {
     const int jl = c0 + lane;
     const bool surv =
         lane < gw && jl < cnt && !(key_lower_bound(s_a[jl], s_b[jl].x, s_e[jl], R) > thr);
