@@ -38,6 +38,7 @@
 // pass C re-tests membership per (candidate, pixel).
 // Nothing is stored between forward and adjoint.
 #pragma once
+#include <utility>
 #include <type_traits>
 
 #include "internal.h"
@@ -231,6 +232,43 @@ __device__ __forceinline__ void insert_key(float (&tq)[A], float& x) {
   }
 }
 
+// Ascending sort of v[0..A-1]: Batcher's odd-even merge network for the next
+// power of two, without the comparators that meet a wire >= A (those wires
+// would hold +inf and never move). The comparator table is built at compile
+// time and applied by a fold, so every index is a constant (registers only).
+struct SortNet {
+  int lo[64], hi[64], n;
+};
+__host__ __device__ constexpr SortNet make_sort_net(int A) {
+  SortNet t{};
+  t.n = 0;
+  for (int p = 1; p < A; p *= 2)
+    for (int k = p; k >= 1; k /= 2)
+      for (int j = k % p; j + k < A; j += 2 * k)
+        for (int i = 0; i < k; ++i)
+          if (i + j + k < A && (i + j) / (2 * p) == (i + j + k) / (2 * p)) {
+            t.lo[t.n] = i + j;
+            t.hi[t.n] = i + j + k;
+            ++t.n;
+          }
+  return t;
+}
+template <int A, size_t... C>
+__device__ __forceinline__ void apply_sort_net(float (&v)[A], std::index_sequence<C...>) {
+  constexpr SortNet t = make_sort_net(A);
+  auto cx = [](float& x, float& y) {
+    const float lo = fminf(x, y);
+    y = fmaxf(x, y);
+    x = lo;
+  };
+  (cx(v[t.lo[C]], v[t.hi[C]]), ...);
+}
+template <int A>
+__device__ __forceinline__ void sort_network(float (&v)[A]) {
+  static_assert(A <= 16, "at most 63 comparators are tabulated");
+  apply_sort_net<A>(v, std::make_index_sequence<make_sort_net(A).n>{});
+}
+
 // Per-pixel result of pass B.
 template <int NCR>
 struct PixelBlend {
@@ -346,21 +384,15 @@ __device__ __forceinline__ void culled_keys(const RenderParams& p, int cnt, floa
   float thr = F_INF;  // no lane of the block can use a key above this
   int c0 = 0, gw = 16;
   if (K > 0) {
-    // the first A candidates (nearest first) fill the empty top K: the k-th
-    // insertion meets only slots 0..k, the later slots still holding +inf,
-    // and drops nothing (a NaN key from a corrupt entry inserts nothing)
+    // the first A candidates (nearest first) fill the empty top K, sorted by
+    // a network; nothing drops (a NaN key from a corrupt entry counts as +inf)
 #pragma unroll
     for (int k = 0; k < A; ++k) {
       const float4 a = s_a[k];
       const float q = k < cnt ? rank_key(px, py, a.x, a.y, a.z, a.w, s_b[k].x) : F_INF;
-      float x = q < F_INF ? q : F_INF;
-#pragma unroll
-      for (int s2 = 0; s2 <= k; ++s2) {
-        const float lo = fminf(tq[s2], x);
-        x = fmaxf(tq[s2], x);
-        tq[s2] = lo;
-      }
+      tq[k] = q < F_INF ? q : F_INF;
     }
+    sort_network<A>(tq);
     c0 = A;
     gw = 32;
     thr = warp_max_key(live ? tq[A - 1] : 0.0f);
