@@ -641,15 +641,32 @@ __device__ __forceinline__ void emit_grad(const RenderParams& p, const TileCtx& 
   const float dT1 = T[2] * c2 + T[4] * s2 + 2.0f * T[3] * sc;
   const float dT2 = T[2] * s2 + T[4] * c2 - 2.0f * T[3] * sc;
   const float d_th = (T1 - T2) * (2.0f * sc * (T[4] - T[2]) + 2.0f * (c2 - s2) * T[3]);
-  float* gdst = p.grad + (int64_t)gid * (5 + n);
-  atomicAdd(gdst + 0, d_mx * (float)t.W);
-  atomicAdd(gdst + 1, d_my * (float)t.H);
-  atomicAdd(gdst + 2, d_th);
-  atomicAdd(gdst + 3, 2.0f * t1 * dT1);
-  atomicAdd(gdst + 4, 2.0f * t2 * dT2);
+  float v[5 + NCR];
+  v[0] = d_mx * (float)t.W;
+  v[1] = d_my * (float)t.H;
+  v[2] = d_th;
+  v[3] = 2.0f * t1 * dT1;
+  v[4] = 2.0f * t2 * dT2;
 #pragma unroll
-  for (int c = 0; c < NCR; ++c)
-    if (NC > 0 || c < n) atomicAdd(gdst + 5 + c, -2.0f * Tc[c]);  // w g / Z
+  for (int c = 0; c < NCR; ++c) v[5 + c] = -2.0f * Tc[c];  // w g / Z
+  float* gdst = p.grad + (int64_t)gid * (5 + n);
+  // a fixed row of 4m (2m) floats on a 16 (8) byte aligned array takes
+  // vector atomics (sm_90+); anything else one float at a time
+  constexpr int NP = 5 + NCR;
+  const uintptr_t al = reinterpret_cast<uintptr_t>(p.grad);
+  if (NC > 0 && NP % 4 == 0 && (al & 15u) == 0) {
+#pragma unroll
+    for (int k = 0; k < NP; k += 4)
+      atomicAdd(reinterpret_cast<float4*>(gdst + k), make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]));
+  } else if (NC > 0 && NP % 2 == 0 && (al & 7u) == 0) {
+#pragma unroll
+    for (int k = 0; k < NP; k += 2)
+      atomicAdd(reinterpret_cast<float2*>(gdst + k), make_float2(v[k], v[k + 1]));
+  } else {
+#pragma unroll
+    for (int k = 0; k < NP; ++k)
+      if (NC > 0 || k < 5 + n) atomicAdd(gdst + k, v[k]);
+  }
 }
 
 __device__ __forceinline__ int block_scan_int(int v, int* scratch, int& total) {
