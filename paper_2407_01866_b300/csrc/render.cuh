@@ -615,7 +615,7 @@ __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   // entries each); the chunked path's (tau, cut-off) per pixel
   L.mask = o;   o += 8 * NT;
   L.coff = o;   o += CH + 1;              // first pair of every candidate
-  L.loss = (o + 1) & ~1; o = L.loss + 2 * NWB + 2;  // doubles
+  L.loss = o;   o += NWB;               // per-warp loss partials
   L.scan = o;   o += 34;                  // integer block-scan scratch
   L.total = o;
   return L;
@@ -979,7 +979,7 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   // per (warp block, candidate) counts of pass B, then first pair slots; after
   // (ex, ey), in pass C's sums' storage, which is free until its loop
   unsigned* s_cnt = reinterpret_cast<unsigned*>(s_slot_a) + 2 * CH;
-  double* s_loss = reinterpret_cast<double*>(smem + SL.loss);
+  float* s_loss = smem + SL.loss;
 
   const int2 lp = pixel_of<TILE>(threadIdx.x);
   const int x = t.x0 + lp.x, y = t.y0 + lp.y;
@@ -1044,15 +1044,18 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   // membership from (tau, cut-off)
   const bool flat = fast && K > 0;
   if (!flat) s_ps1[threadIdx.x] = make_float2(live ? r.tau : -F_INF, __int_as_float(r.gcut));
+  // per-warp and per-tile partial sums (at most 32 and 256 n terms |d| <= 1)
+  // in float32, one float64 atomic per tile (FP64 arithmetic is slow here)
   if (!p.grad_img) {
-    const double l = warp_sum<double>((double)loss);
+    const float l = warp_sum<float>(loss);
     if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = l;
   }
   __syncthreads();
   if (!p.grad_img && threadIdx.x == 0) {
-    double tot = 0.0;
+    float tot = 0.0f;
+#pragma unroll
     for (int i = 0; i < NT / 32; ++i) tot += s_loss[i];
-    if (tot != 0.0) atomicAdd(t.loss_acc, tot);
+    if (tot != 0.0f) atomicAdd(t.loss_acc, (double)tot);
   }
 
   // ---- pass C: candidate-major accumulation of the adjoint
