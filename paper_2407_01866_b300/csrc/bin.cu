@@ -383,6 +383,26 @@ __global__ void __launch_bounds__(256) k_segsort_big(unsigned int* vals, unsigne
     const int L = (int)(b - a);
     for (int c0 = 0; c0 < L; c0 += SEG_BIG_CHUNK) {
       const int n = min(SEG_BIG_CHUNK, L - c0);
+      if (n <= 2 * 256) {
+        // rank sort, two entries per thread: an entry's place is the number
+        // of smaller entries (equal ones, only in a corrupt list, by position)
+        __syncthreads();
+        const int i0 = threadIdx.x, i1 = threadIdx.x + 256;
+        const unsigned int v0 = i0 < n ? vals[a + c0 + i0] : 0u;
+        const unsigned int v1 = i1 < n ? vals[a + c0 + i1] : 0u;
+        if (i0 < n) sh[i0] = v0;
+        if (i1 < n) sh[i1] = v1;
+        __syncthreads();
+        int r0 = 0, r1 = 0;
+        for (int j = 0; j < n; ++j) {
+          const unsigned int x = sh[j];
+          r0 += (x < v0 || (x == v0 && j < i0)) ? 1 : 0;
+          r1 += (x < v1 || (x == v1 && j < i1)) ? 1 : 0;
+        }
+        if (i0 < n) vals[a + c0 + r0] = v0;
+        if (i1 < n) vals[a + c0 + r1] = v1;
+        continue;
+      }
       int P = 64;  // bitonic width: the chunk rounded up to a power of two
       while (P < n) P <<= 1;
       __syncthreads();
