@@ -9,20 +9,22 @@ namespace igs {
 
 namespace {
 
+// Adam's bias correction 1 - beta^t in float32, from omb = 1 - beta: it is
+// -expm1(t log1p(-omb)), within a few ulp of the float64 value. Every thread
+// computes it (no float64 pow: on this part the FP64 pipe is narrow, and a
+// per-CTA float64 pow behind a barrier stalled every CTA of the update).
+__device__ __forceinline__ float one_minus_pow(float omb, int t) {
+  return -expm1f((float)t * log1pf(-omb));
+}
+
 // One thread per Gaussian row: the column of each element (and so its learning
 // rate and clamp) is known without a division, and a row's 5+n floats are
 // contiguous, so a warp touches 32 consecutive rows.
 template <int NP>
 __global__ void __launch_bounds__(256) k_adam(AdamParams a) {
-  __shared__ float s_bc[2];
-  if (threadIdx.x == 0) {
-    const int step = *a.step + 1;
-    s_bc[0] = (float)(1.0 - pow(a.b1d, (double)step));
-    s_bc[1] = (float)(1.0 - pow(a.b2d, (double)step));
-  }
-  __syncthreads();
-  const float inv_bc1 = 1.0f / s_bc[0];
-  const float inv_bc2 = 1.0f / s_bc[1];
+  const int step = *a.step + 1;
+  const float inv_bc1 = 1.0f / one_minus_pow(a.omb1, step);
+  const float inv_bc2 = 1.0f / one_minus_pow(a.omb2, step);
   const int np = NP > 0 ? NP : 5 + a.n;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.N;
        r += (int64_t)gridDim.x * blockDim.x) {
@@ -51,15 +53,9 @@ __global__ void __launch_bounds__(256) k_adam(AdamParams a) {
 template <int NP>
 __global__ void __launch_bounds__(256) k_adam_v4(AdamParams a) {
   static_assert(NP % 4 == 0, "float4 rows");
-  __shared__ float s_bc[2];
-  if (threadIdx.x == 0) {
-    const int step = *a.step + 1;
-    s_bc[0] = (float)(1.0 - pow(a.b1d, (double)step));
-    s_bc[1] = (float)(1.0 - pow(a.b2d, (double)step));
-  }
-  __syncthreads();
-  const float inv_bc1 = 1.0f / s_bc[0];
-  const float inv_bc2 = 1.0f / s_bc[1];
+  const int step = *a.step + 1;
+  const float inv_bc1 = 1.0f / one_minus_pow(a.omb1, step);
+  const float inv_bc2 = 1.0f / one_minus_pow(a.omb2, step);
   const int64_t n4 = a.N * NP / 4;
   float4* P4 = reinterpret_cast<float4*>(a.P);
   const float4* G4 = reinterpret_cast<const float4*>(a.G);

@@ -353,8 +353,6 @@ int igs_adam_update(const igs_fit_state* st, const igs_config* cfg, igs_stream s
   a.b2 = (float)cfg->beta2;
   a.omb1 = (float)(1.0 - cfg->beta1);
   a.omb2 = (float)(1.0 - cfg->beta2);
-  a.b1d = cfg->beta1;
-  a.b2d = cfg->beta2;
   a.eps = cfg->eps;
   a.theta_min = cfg->theta_min;
   a.theta_max = cfg->theta_max;

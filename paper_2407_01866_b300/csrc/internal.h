@@ -131,7 +131,6 @@ struct AdamParams {
   int64_t N;
   int n;
   float lr_mu, lr_theta, lr_t, lr_c, b1, b2, omb1, omb2, eps;
-  double b1d, b2d;  // for the bias corrections
   float theta_min, theta_max, t_min, t_max, mu_min, mu_max;
 };
 cudaError_t launch_adam(const AdamParams& a, cudaStream_t s);
