@@ -36,11 +36,11 @@ SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2032.0
 # DRAM bytes (read + write) of one fused forward + L1 + adjoint launch on the
-# fitted 2048^2 RGB state, from the ncu capture summarised in
-# profiles/k_render_fit2048_rgb.md (64.64 MB read + 1.90 MB written); the
+# fitted 2048^2 RGB state, from an ncu capture of that launch
+# (dram__bytes_read.sum 64.54 MB + dram__bytes_write.sum 1.77 MB); the
 # 2048^2 RGB workload only
-FUSED_TRAFFIC_2048_RGB = 66.54e6
-# library kernels of one fit step (profiles/launches_fit2048_rgb.md): finalize,
+FUSED_TRAFFIC_2048_RGB = 66.31e6
+# library kernels of one fit step (the ncu launch list of the bench): finalize,
 # preprocess, 2 wide-Gaussian passes, 3 scan passes, emit, 2 segment sorts,
 # ranges, tile evaluations, fused adjoint, Adam
 KERNELS_PER_FIT_STEP = 14
