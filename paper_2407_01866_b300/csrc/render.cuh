@@ -121,9 +121,12 @@ __device__ __forceinline__ float warp_max_key(float v) {
   return __uint_as_float(__reduce_max_sync(FULL_MASK, __float_as_uint(fmaxf(v, 0.0f))));
 }
 
-// Chunked path: stage list entries [base, base+cnt) in list order. Colours
-// of staged candidates live in shared memory, channel-major s_col[c * NT + j],
-// when the channel count is a compile-time constant.
+// Colours of staged candidates live in shared memory, candidate-major
+// s_col[j * col_stride(NC) + c], when the channel count is a compile-time
+// constant; three channels are padded to a float4 (one 16-byte load).
+__host__ __device__ constexpr int col_stride(int nc) { return nc == 3 ? 4 : (nc > 0 ? nc : 1); }
+
+// Chunked path: stage list entries [base, base+cnt) in list order.
 template <int NT, int NC>
 __device__ __forceinline__ void stage_chunk(const RenderParams& p, int base, int cnt,
                                             float4* s_a, float2* s_b, float* s_col) {
@@ -137,14 +140,14 @@ __device__ __forceinline__ void stage_chunk(const RenderParams& p, int base, int
       if (NC > 0) {
 #pragma unroll
         for (int c = 0; c < (NC > 0 ? NC : 1); ++c)
-          s_col[c * NT + j] = p.color[(int64_t)gid * NC + c];
+          s_col[j * col_stride(NC) + c] = p.color[(int64_t)gid * NC + c];
       }
     } else {  // corrupt list entry: a NaN key is never selected
       s_a[j] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
       s_b[j] = make_float2(0.f, __int_as_float(-1));
       if (NC > 0) {
 #pragma unroll
-        for (int c = 0; c < (NC > 0 ? NC : 1); ++c) s_col[c * NT + j] = 0.0f;
+        for (int c = 0; c < (NC > 0 ? NC : 1); ++c) s_col[j * col_stride(NC) + c] = 0.0f;
       }
       atomicOr(&p.status->flags, FLAG_INTERNAL);
     }
@@ -197,7 +200,7 @@ __device__ __forceinline__ void stage_sorted(const RenderParams& p, int base, in
       s_e[r] = make_float2(0.5f / g.a.z, 0.5f / g.b.x);
       if (NC > 0) {
 #pragma unroll
-        for (int c = 0; c < NCS; ++c) s_col[c * NT + r] = col[c];
+        for (int c = 0; c < NCS; ++c) s_col[r * col_stride(NC) + c] = col[c];
       }
     } else {  // corrupt list entry: a NaN key is never selected
       s_a[r] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
@@ -205,7 +208,7 @@ __device__ __forceinline__ void stage_sorted(const RenderParams& p, int base, in
       s_e[r] = make_float2(0.f, 0.f);
       if (NC > 0) {
 #pragma unroll
-        for (int c = 0; c < NCS; ++c) s_col[c * NT + r] = 0.0f;
+        for (int c = 0; c < NCS; ++c) s_col[r * col_stride(NC) + c] = 0.0f;
       }
       atomicOr(&p.status->flags, FLAG_INTERNAL);
     }
@@ -216,8 +219,27 @@ __device__ __forceinline__ void stage_sorted(const RenderParams& p, int base, in
 template <int NT, int NC>
 __device__ __forceinline__ float staged_colour(const RenderParams& p, const float* s_col,
                                                const float2* s_b, int j, int c) {
-  if (NC > 0) return s_col[c * NT + j];
+  if (NC > 0) return s_col[j * col_stride(NC) + c];
   return p.color[(int64_t)__float_as_int(s_b[j].y) * p.n + c];
+}
+
+// All channels of staged candidate j (one 16-byte load for 3 or 4 channels).
+template <int NT, int NC>
+__device__ __forceinline__ void staged_colours(const RenderParams& p, const float* s_col,
+                                               const float2* s_b, int j,
+                                               float (&cc)[Chan<NC>::R]) {
+  if (NC == 3 || NC == 4) {
+    const float4 v = reinterpret_cast<const float4*>(s_col)[j];
+    cc[0] = v.x;
+    cc[1] = v.y;
+    cc[2] = v.z;
+    if (NC == 4) cc[NC == 4 ? 3 : 0] = v.w;
+  } else {
+    const int n = nchan<NC>(p);
+#pragma unroll
+    for (int c = 0; c < Chan<NC>::R; ++c)
+      cc[c] = (NC > 0 || c < n) ? staged_colour<NT, NC>(p, s_col, s_b, j, c) : 0.0f;
+  }
 }
 
 // Sorted insertion of key x into tq[0..A-1] (ascending), the largest key
@@ -351,10 +373,11 @@ __device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, fl
         if (win) {
           const float w = blend_weight(r.q0, q);  // exactly 1 at q = q_min
           r.Z += w;
+          float cc[NCR];
+          staged_colours<CH, NC>(p, s_col, s_b, j, cc);
 #pragma unroll
           for (int c = 0; c < NCR; ++c)
-            if (NC > 0 || c < n)
-              r.cr[c] = fmaf(w, staged_colour<CH, NC>(p, s_col, s_b, j, c), r.cr[c]);
+            if (NC > 0 || c < n) r.cr[c] = fmaf(w, cc[c], r.cr[c]);
         }
       }
     }
@@ -515,10 +538,11 @@ __device__ __forceinline__ void culled_blend(const RenderParams& p, int cnt, flo
       if (win) {
         const float w = blend_weight(r.q0, q);  // exactly 1 at q = q_min
         r.Z += w;
+        float cc[NCR];
+        staged_colours<CH, NC>(p, s_col, s_b, j, cc);
 #pragma unroll
         for (int c = 0; c < NCR; ++c)
-          if (NC > 0 || c < n)
-            r.cr[c] = fmaf(w, staged_colour<CH, NC>(p, s_col, s_b, j, c), r.cr[c]);
+          if (NC > 0 || c < n) r.cr[c] = fmaf(w, cc[c], r.cr[c]);
       }
     };
     while (m) {
@@ -547,7 +571,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(RenderParams p) {
   __shared__ float2 s_b[NT];
   __shared__ float2 s_e[NT];
   __shared__ __align__(16) unsigned s_key[2 * NT];
-  __shared__ float s_col[NT * (NC > 0 ? NC : 1)];
+  __shared__ __align__(16) float s_col[NT * col_stride(NC)];
   const int tile_id = blockIdx.x;
   const int x0 = (tile_id % p.tiles_x) * TILE, y0 = (tile_id / p.tiles_x) * TILE;
   const int2 lp = pixel_of<TILE>(threadIdx.x);
@@ -603,7 +627,7 @@ __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   int o = 0;
   L.a = o;      o += 4 * CH;              // float4 (mx, my, A00, B)
   L.b = o;      o += 2 * CH;              // float2 (A11, index)
-  L.col = o;    o = al4(o + n * CH);      // staged colours, channel-major
+  L.col = o;    o = al4(o + col_stride(n) * CH);  // staged colours (16-byte aligned)
   L.ps0 = o;    o += 4 * NT;              // float4 (px, py, q0, beta) per pixel
   L.gh = o;     o = al4(o + n * NT);      // per-pixel -g/(2Z), channel-major
   // pass C per-candidate sums A_j; before them (ex, ey) of the staged
@@ -778,11 +802,7 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
     float4 a = s_a[j];
     float a11 = s_b[j].x;
     float cc[NCR];
-    auto load_colour = [&](int jj) {
-#pragma unroll
-      for (int c = 0; c < NCR; ++c)
-        cc[c] = (NC > 0 || c < n) ? staged_colour<CH, NC>(p, s_col, s_b, jj, c) : 0.0f;
-    };
+    auto load_colour = [&](int jj) { staged_colours<CH, NC>(p, s_col, s_b, jj, cc); };
     load_colour(j);
     float T[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     float Tc[NCR];
