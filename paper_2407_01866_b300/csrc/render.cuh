@@ -223,6 +223,27 @@ __device__ __forceinline__ float staged_colour(const RenderParams& p, const floa
   return p.color[(int64_t)__float_as_int(s_b[j].y) * p.n + c];
 }
 
+// Per-pixel factors -g/(2Z) of the adjoint in shared memory: pixel-major,
+// one float4 per pixel, for 3 or 4 channels; channel-major otherwise.
+template <int NC>
+__device__ __forceinline__ int gh_at(int i, int c, int NT) {
+  return (NC == 3 || NC == 4) ? i * 4 + c : c * NT + i;
+}
+template <int NC>
+__device__ __forceinline__ void pixel_gh(const float* s_gh, int i, int n, int NT,
+                                         float (&gh)[Chan<NC>::R]) {
+  if (NC == 3 || NC == 4) {
+    const float4 v = reinterpret_cast<const float4*>(s_gh)[i];
+    gh[0] = v.x;
+    gh[1] = v.y;
+    gh[2] = v.z;
+    if (NC == 4) gh[NC == 4 ? 3 : 0] = v.w;
+  } else {
+#pragma unroll
+    for (int c = 0; c < Chan<NC>::R; ++c) gh[c] = (NC > 0 || c < n) ? s_gh[c * NT + i] : 0.0f;
+  }
+}
+
 // All channels of staged candidate j (one 16-byte load for 3 or 4 channels).
 template <int NT, int NC>
 __device__ __forceinline__ void staged_colours(const RenderParams& p, const float* s_col,
@@ -629,7 +650,7 @@ __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   L.b = o;      o += 2 * CH;              // float2 (A11, index)
   L.col = o;    o = al4(o + col_stride(n) * CH);  // staged colours (16-byte aligned)
   L.ps0 = o;    o += 4 * NT;              // float4 (px, py, q0, beta) per pixel
-  L.gh = o;     o = al4(o + n * NT);      // per-pixel -g/(2Z), channel-major
+  L.gh = o;     o = al4(o + col_stride(n) * NT);  // per-pixel -g/(2Z) (16-byte aligned)
   // pass C per-candidate sums A_j; before them (ex, ey) of the staged
   // candidates, followed by pass B's NWB x CH counts (2 + NWB <= 10 <= 2 np
   // words per candidate, as np >= 6 and CH <= NT, so they end inside slot_b)
@@ -833,12 +854,11 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
       const float q = __fmaf_rn(h, dx, __fmul_rn(__fmul_rn(a11, dy), dy));
       const float w = blend_weight(s0.z, q);
       float gh[NCR];
+      pixel_gh<NC>(s_gh, i, n, NT, gh);
       float gd = -s0.w;
 #pragma unroll
-      for (int c = 0; c < NCR; ++c) {
-        gh[c] = (NC > 0 || c < n) ? s_gh[c * NT + i] : 0.0f;
+      for (int c = 0; c < NCR; ++c)
         if (NC > 0 || c < n) gd = fmaf(gh[c], cc[c], gd);
-      }
       const float Gq = w * gd;
       const float e1 = Gq * dx, e2 = Gq * dy;
       T[0] += e1;
@@ -932,7 +952,7 @@ __device__ __forceinline__ void chunked_pass_c(const RenderParams& p, const Tile
           float gd = -s0.w;
 #pragma unroll
           for (int c = 0; c < NCR; ++c)
-            if (NC > 0 || c < n) gd = fmaf(s_gh[c * NT + i], cc[c], gd);
+            if (NC > 0 || c < n) gd = fmaf(s_gh[gh_at<NC>(i, c, NT)], cc[c], gd);
           const float Gq = w * gd;
           const float e1 = Gq * dx, e2 = Gq * dy;
           S1 += e1;
@@ -942,7 +962,7 @@ __device__ __forceinline__ void chunked_pass_c(const RenderParams& p, const Tile
           S22 = fmaf(e2, dy, S22);
 #pragma unroll
           for (int c = 0; c < NCR; ++c)
-            if (NC > 0 || c < n) Sc[c] = fmaf(w, s_gh[c * NT + i], Sc[c]);
+            if (NC > 0 || c < n) Sc[c] = fmaf(w, s_gh[gh_at<NC>(i, c, NT)], Sc[c]);
         }
       }
     }
@@ -1056,7 +1076,7 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
       }
       const float gh = -0.5f * g * iz;  // dL/dq_k = w_k * (sum_c gh_c c_k,c - beta)
       if (p.normalize) beta = fmaf(gh, r.cr[c], beta);
-      s_gh[c * NT + threadIdx.x] = gh;
+      s_gh[gh_at<NC>(threadIdx.x, c, NT)] = gh;
     }
   }
   s_ps0[threadIdx.x] = make_float4(px, py, r.q0, beta);
