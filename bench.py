@@ -37,9 +37,9 @@ FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2032.0
 # DRAM bytes (read + write) of one fused forward + L1 + adjoint launch on the
 # fitted 2048^2 RGB state, from an ncu capture of that launch
-# (dram__bytes_read.sum 64.54 MB + dram__bytes_write.sum 1.77 MB); the
+# (dram__bytes_read.sum 64.64 MB + dram__bytes_write.sum 1.69 MB); the
 # 2048^2 RGB workload only
-FUSED_TRAFFIC_2048_RGB = 66.31e6
+FUSED_TRAFFIC_2048_RGB = 66.33e6
 # library kernels of one fit step (the ncu launch list of the bench): finalize,
 # preprocess, 2 wide-Gaussian passes, 3 scan passes, emit, 2 segment sorts,
 # ranges, tile evaluations, fused adjoint, Adam
