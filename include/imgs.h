@@ -180,7 +180,11 @@ int igs_render_forward(const igs_bins* bins, const igs_config* cfg,
  * otherwise L = mean |c_r - c_t| over H*W*n against d_target [n][H][W]
  * (d|z|/dz = sign(z), sign(0) = 0) and sum |c_r - c_t| is added to the
  * status block's loss_sum. The gradient is with respect to the stored
- * parameter values (float16/bfloat16 storage: the values upcast exactly). */
+ * parameter values (float16/bfloat16 storage: the values upcast exactly).
+ * Tiles add their contributions with float atomics (16-byte vector atomics
+ * where d_grad is 16-byte aligned and a row is a multiple of 4 floats), so
+ * the rounding order of d_grad varies between calls; the loss is summed in
+ * float32 per tile and in float64 across tiles. */
 int igs_render_backward(const igs_gaussians* g, const igs_bins* bins,
                         const igs_config* cfg, const float* d_grad_img,
                         const float* d_target, float* d_grad, igs_stream stream);
