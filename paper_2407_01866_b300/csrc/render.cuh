@@ -11,9 +11,11 @@
 // candidate's ranking key at the tile centre, nearest first. The order
 // decides only how much work is skipped, never which Gaussians win.
 //
-//   pass A  keys only: every pixel keeps its K smallest ranking keys q with a
-//           min/max insertion network, run only when some lane of the warp
-//           improves on its K-th key (warp vote). Before 32 candidates are
+//   pass A  keys only: the first K candidates fill every pixel's top K
+//           through a sorting network; after them each pixel keeps its K
+//           smallest ranking keys q with a min/max insertion network, run
+//           only when some lane of the warp improves on its K-th key (warp
+//           vote). Before 32 candidates are
 //           evaluated per pixel, the warp tests them lane-parallel against a
 //           lower bound of q over its 8 x 4 block: a candidate whose bound
 //           exceeds the K-th key of every pixel of the block cannot enter any
@@ -25,13 +27,15 @@
 //           smallest indices, as the (q, index) order of the top-K demands).
 //           Candidates are culled against the block's largest tau. Winners
 //           are blended with w = exp(-(q - q_min)/2) (Eq. 5); the adjoint
-//           records the ballot of winning pixels per (warp, candidate).
-//   pass C  (adjoint only) the winning (candidate, pixel) pairs are split
-//           evenly over the CTA's threads; each accumulates dL/dq moments in
-//           registers and leaves one partial sum per candidate it touched in
-//           a shared-memory slot with a single writer; one thread per
-//           candidate adds its slots and turns them into parameter gradients
-//           with 5+n global atomics.
+//           records every pixel's winners (candidate, rank among the warp's
+//           winning pixels of it) and per (warp, candidate) their number.
+//   pass C  (adjoint only) a counting sort of those records lays out the
+//           winning (candidate, pixel) pairs candidate-major; the pairs are
+//           split evenly over the CTA's threads; each accumulates dL/dq
+//           moments in registers and leaves one partial sum per candidate it
+//           touched in a shared-memory slot with a single writer; one thread
+//           per candidate adds its slots and turns them into parameter
+//           gradients with global (vector) atomics.
 //
 // Longer lists take the chunked path: passes A and B stream the list in
 // ascending index order (equal keys at tau are admitted in that order), and
@@ -638,7 +642,7 @@ struct TileCtx {
 // Dynamic shared-memory layout of the adjoint kernel (in 4-byte words), for
 // NT pixels, n channels and CH Gaussians per stage (64 <= CH <= NT).
 struct BwdSmem {
-  int a, b, col, ps0, gh, slot_a, slot_b, mask, coff, loss, scan, total;
+  int a, b, col, ps0, gh, slot_a, slot_b, win, coff, loss, scan, total;
 };
 __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   const int NWB = NT / 32;
@@ -658,7 +662,7 @@ __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   L.slot_b = o; o = al4(o + np * NT);     // pass C per-thread sums B_t; rank keys before
   // pass B's 16-bit winner records, then pass C's pair table (<= 16 NT
   // entries each); the chunked path's (tau, cut-off) per pixel
-  L.mask = o;   o += 8 * NT;
+  L.win = o;    o += 8 * NT;
   L.coff = o;   o += CH + 1;              // first pair of every candidate
   L.loss = o;   o += NWB;               // per-warp loss partials
   L.scan = o;   o += 34;                  // integer block-scan scratch
@@ -1014,8 +1018,8 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   float2* s_e = reinterpret_cast<float2*>(s_slot_a);      // until pass C
   unsigned* s_key = reinterpret_cast<unsigned*>(s_slot_b);  // while staging
   // pass B's per-pixel records, then pass C's pair table (fast path)
-  unsigned short* s_win = reinterpret_cast<unsigned short*>(smem + SL.mask);
-  float2* s_ps1 = reinterpret_cast<float2*>(smem + SL.mask);  // chunked path only
+  unsigned short* s_win = reinterpret_cast<unsigned short*>(smem + SL.win);
+  float2* s_ps1 = reinterpret_cast<float2*>(smem + SL.win);  // chunked path only
   // per (warp block, candidate) counts of pass B, then first pair slots; after
   // (ex, ey), in pass C's sums' storage, which is free until its loop
   unsigned* s_cnt = reinterpret_cast<unsigned*>(s_slot_a) + 2 * CH;
