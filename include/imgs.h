@@ -307,10 +307,13 @@ int igs_autotune_batch(const igs_fit_state* st, const float* d_targets,
  *   rejected with IGS_ERR_CAPACITY before any GPU work; if the
  *   intersections found on the GPU do not fit, the call returns
  *   IGS_ERR_CAPACITY after rendering and the image is incomplete.
+ * - The scratch is sized for binning only (igs_preprocess_bin's sections);
+ *   an SSIM weight in cfg costs it nothing.
  * - The call synchronises `stream` at its end to read the status block.
- * - The first call on a device looks up the array's device address (once
- *   per device, with that device current); make that first call before
- *   any stream capture.
+ * - Every call looks up the array's device address on the current device
+ *   (cudaGetSymbolAddress), so the address stays right after a device
+ *   reset; the first call on a device also loads the library's module
+ *   there, so make that first call before any stream capture.
  * - All calls share the one array, which keeps the last call's contents;
  *   every word a call reads is cleared or written by that call first.
  *   Calls that overlap on the GPU (other streams, other host threads) race

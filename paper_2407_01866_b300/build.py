@@ -1,9 +1,11 @@
-"""Build libimgs.so (all CUDA sources, sm_103a) in-tree.
+"""Build libimgs.so (all CUDA sources, sm_103a) and libigs_peaks.so in-tree.
 
 Usage: python -m paper_2407_01866_b300.build [--force] [-j N]
 Each .cu under csrc/ compiles to an object under _build/ in parallel; the
 objects link into paper_2407_01866_b300/libimgs.so. A source rebuilds when it
-or any header under csrc/ or include/ is newer than its object.
+or any header under csrc/ or include/ is newer than its object. The
+throughput probes of the roofline (peaks/peaks.cu, include/igs_peaks.h)
+build into their own paper_2407_01866_b300/libigs_peaks.so.
 """
 import argparse
 import concurrent.futures as cf
@@ -18,6 +20,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libimgs.so")
+PEAKS_SRC = os.path.join(PKG, "peaks", "peaks.cu")
+PEAKS_LIB = os.path.join(PKG, "libigs_peaks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -60,8 +64,16 @@ def build(force=False, jobs=None, verbose=False):
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n$ {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
+    peaks_newest = max(os.path.getmtime(PEAKS_SRC),
+                       os.path.getmtime(os.path.join(INCLUDE, "igs_peaks.h")))
+    if force or not os.path.exists(PEAKS_LIB) or os.path.getmtime(PEAKS_LIB) < peaks_newest:
+        cmd = [NVCC] + FLAGS + ["-shared", PEAKS_SRC, "-o", PEAKS_LIB]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed:\n$ {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
     if verbose:
         print(LIB)
+        print(PEAKS_LIB)
     return LIB
 
 

@@ -2,8 +2,9 @@
 //
 // The images' Gaussians are concatenated (in image order) and binned in one
 // pass over a concatenated tile space: image b owns global tiles
-// [tile_off[b], tile_off[b+1]), so one stable radix sort by global tile id
-// gives every image its own S_j. One persistent launch of the fused
+// [tile_off[b], tile_off[b+1]), and the per-tile counters, their scan and the
+// atomic slots of the binning give every image its own S_j. One persistent
+// launch of the fused
 // forward + L1 + adjoint kernel then pulls tiles of all images from a device
 // counter, which balances small and large images on the 148 SMs; Adam runs
 // once over all parameters. The per-image tables live in the workspace after

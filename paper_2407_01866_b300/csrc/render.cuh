@@ -11,24 +11,25 @@
 // candidate's ranking key at the tile centre, nearest first. The order
 // decides only how much work is skipped, never which Gaussians win.
 //
-//   pass A  keys only: the first K candidates fill every pixel's top K
-//           through a sorting network; after them each pixel keeps its K
-//           smallest ranking keys q with a min/max insertion network, run
-//           only when some lane of the warp improves on its K-th key (warp
-//           vote). Before 32 candidates are
-//           evaluated per pixel, the warp tests them lane-parallel against a
-//           lower bound of q over its 8 x 4 block: a candidate whose bound
-//           exceeds the K-th key of every pixel of the block cannot enter any
-//           top K and is skipped. Gives q_min, the K-th key tau and the
-//           smallest key left out of the top K.
-//   pass B  membership and blend: a candidate wins iff q < tau, or q == tau
-//           and its index is at most the pixel's tie cut-off (no limit unless
-//           a key equal to tau was left out; then the cut-off admits the
-//           smallest indices, as the (q, index) order of the top-K demands).
-//           Candidates are culled against the block's largest tau. Winners
-//           are blended with w = exp(-(q - q_min)/2) (Eq. 5); the adjoint
-//           records every pixel's winners (candidate, rank among the warp's
-//           winning pixels of it) and per (warp, candidate) their number.
+//   pass A  each pixel keeps the K smallest packed keys (the binary32
+//           ranking key with its low 8 bits replaced by the staged slot):
+//           the first K candidates fill the top K through a sorting network,
+//           later ones enter through a min/max insertion network, run only
+//           when some lane of the warp improves (warp vote). Before
+//           candidates are evaluated per pixel, the warp tests them
+//           lane-parallel against a lower bound of the key over its 8 x 4
+//           block, and re-tests the survivors as the threshold falls: a
+//           candidate whose bound exceeds the K-th key of every pixel of the
+//           block cannot enter any top K and is skipped. The packed top K is
+//           the exact (key, index) top K unless the K-th and (K+1)-th packed
+//           keys share their upper 24 bits (or the K-th is negative); a warp
+//           with such a pixel recomputes its selection exactly (the float
+//           pass A, the tie cut-off and a membership pass).
+//   blend   the winners' slots come out of pass A: their keys are recomputed
+//           exactly and blended with w = exp(-(q - q_min)/2) (Eq. 5). The
+//           adjoint also records each winner as (slot, rank of the pixel
+//           among this warp's pixels that won the slot), from per-warp lane
+//           masks of every slot's winners.
 //   pass C  (adjoint only) a counting sort of those records lays out the
 //           winning (candidate, pixel) pairs candidate-major; the pairs are
 //           split evenly over the CTA's threads; each accumulates dL/dq
@@ -37,10 +38,11 @@
 //           per candidate adds its slots and turns them into parameter
 //           gradients with global (vector) atomics.
 //
-// Longer lists take the chunked path: passes A and B stream the list in
-// ascending index order (equal keys at tau are admitted in that order), and
-// pass C re-tests membership per (candidate, pixel).
-// Nothing is stored between forward and adjoint.
+// K = 0 (every candidate of S_j wins) keeps float keys: pass A finds q_min
+// and pass B blends every candidate. Longer lists take the chunked path:
+// passes A and B stream the list in ascending index order (equal keys at tau
+// are admitted in that order), and pass C re-tests membership per
+// (candidate, pixel). Nothing is stored between forward and adjoint.
 #pragma once
 #include <utility>
 #include <type_traits>
@@ -206,8 +208,8 @@ __device__ __forceinline__ void stage_sorted(const RenderParams& p, int base, in
 #pragma unroll
         for (int c = 0; c < NCS; ++c) s_col[r * col_stride(NC) + c] = col[c];
       }
-    } else {  // corrupt list entry: a NaN key is never selected
-      s_a[r] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
+    } else {  // corrupt list entry: key +inf at every pixel (weight 0 if kept)
+      s_a[r] = make_float4(F_INF, 0.f, 1.f, 0.f);
       s_b[r] = make_float2(0.f, __int_as_float(-1));
       s_e[r] = make_float2(0.f, 0.f);
       if (NC > 0) {
@@ -445,12 +447,14 @@ __device__ __forceinline__ void culled_keys(const RenderParams& p, int cnt, floa
     gw = 32;
     thr = warp_max_key(live ? tq[A - 1] : 0.0f);
   }
-  // (K = 0: a first group of 16 then groups of 32)
+  // (K = 0: a first group of 16 then groups of 32). A lane holds the bound of
+  // one candidate of the group; the survivors are re-tested against the
+  // threshold after every pair, as it only falls.
   for (; c0 < cnt; c0 += gw, gw = 32) {
     const int jl = c0 + lane;
-    const bool surv =
-        lane < gw && jl < cnt && !(key_lower_bound(s_a[jl], s_b[jl].x, s_e[jl], R) > thr);
-    unsigned m = __ballot_sync(FULL_MASK, surv);
+    const float bnd = (lane < gw && jl < cnt) ? key_lower_bound(s_a[jl], s_b[jl].x, s_e[jl], R)
+                                              : F_INF;
+    unsigned m = __ballot_sync(FULL_MASK, !(bnd > thr));
     auto take = [&](float q) {
       if (K == 0) {  // all of S_j: only the smallest key is needed
         tq[0] = fminf(tq[0], q);
@@ -477,6 +481,10 @@ __device__ __forceinline__ void culled_keys(const RenderParams& p, int cnt, floa
       const float q1 = rank_key(px, py, a1.x, a1.y, a1.z, a1.w, b1);
       take(q0);
       if (two) take(q1);
+      if (K > 0) {
+        thr = warp_max_key(live ? tq[A - 1] : 0.0f);
+        m &= __ballot_sync(FULL_MASK, !(bnd > thr));
+      }
     }
     thr = warp_max_key(live ? tq[A - 1] : 0.0f);
   }
@@ -589,8 +597,230 @@ __device__ __forceinline__ void culled_blend(const RenderParams& p, int cnt, flo
   for (int c = 0; c < NCR; ++c) r.cr[c] *= iz;
 }
 
+// ---------------------------------------------------------------------------
+// Fast path with packed keys (K > 0). Pass A keeps, per pixel, the K smallest
+// packed keys: the binary32 ranking key's bits with the low 8 bits replaced
+// by the candidate's staged slot, compared as signed integers. Within one
+// bucket of equal upper 24 bits the packed order is the slot order instead
+// of the (key, index) order; outside it the two orders agree (keys >= 0
+// order like their bits). So the K smallest packed keys are exactly the top K
+// unless the K-th and the (K+1)-th smallest fall in one bucket, or the K-th is
+// negative (a key below 0 from rounding; negative keys order in reverse as
+// integers). The warp then takes the exact path instead: the float pass A,
+// the tie cut-off and a membership pass. Otherwise the winners' slots come
+// straight out of pass A and no candidate is evaluated a second time to find
+// them; only the K winners' keys are recomputed exactly for the blend.
+// ---------------------------------------------------------------------------
+constexpr int PK_NONE = 0x7fffffff;  // empty slot: after every packed key
+
+__device__ __forceinline__ int pack_key(float q, int slot) {
+  return (__float_as_int(q) & ~0xff) | slot;
+}
+
+// Sorted insertion of packed key x into tq[0..A-1] (ascending); the largest
+// drops out into x. PK_NONE inserts nothing.
+template <int A>
+__device__ __forceinline__ void insert_pk(int (&tq)[A], int& x) {
+#pragma unroll
+  for (int k = 0; k < A; ++k) {
+    const int lo = min(tq[k], x);
+    x = max(tq[k], x);
+    tq[k] = lo;
+  }
+}
+
+template <int A, size_t... C>
+__device__ __forceinline__ void apply_sort_net_pk(int (&v)[A], std::index_sequence<C...>) {
+  constexpr SortNet t = make_sort_net(A);
+  auto cx = [](int& x, int& y) {
+    const int lo = min(x, y);
+    y = max(x, y);
+    x = lo;
+  };
+  (cx(v[t.lo[C]], v[t.hi[C]]), ...);
+}
+template <int A>
+__device__ __forceinline__ void sort_network_pk(int (&v)[A]) {
+  static_assert(A <= 16, "at most 63 comparators are tabulated");
+  apply_sort_net_pk<A>(v, std::make_index_sequence<make_sort_net(A).n>{});
+}
+
+// Cull threshold of the packed pass A: the upper end of the bucket of the
+// largest K-th packed key over the warp's live lanes, as a float. A candidate
+// whose key lower bound exceeds it lies in a later bucket than every live
+// lane's K-th packed key, so it can neither enter a top K nor share the K-th
+// bucket.
+__device__ __forceinline__ float pk_threshold(int tk, bool live) {
+  return __int_as_float(__reduce_max_sync(FULL_MASK, live ? (tk | 0xff) : INT_MIN));
+}
+
+// Pass A with packed keys. tq receives the K smallest packed keys (ascending,
+// PK_NONE beyond the list's length), mdrop the smallest packed key evaluated
+// but not kept (PK_NONE if none).
+template <int K>
+__device__ __forceinline__ void packed_keys(int cnt, float px, float py, bool live,
+                                            const float4& R, const float4* s_a,
+                                            const float2* s_b, const float2* s_e, int (&tq)[K],
+                                            int& mdrop) {
+  const int lane = threadIdx.x & 31;
+  // the first K candidates (nearest first) fill the top K through a network
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float4 a = s_a[k];
+    tq[k] = k < cnt ? pack_key(rank_key(px, py, a.x, a.y, a.z, a.w, s_b[k].x), k) : PK_NONE;
+  }
+  sort_network_pk<K>(tq);
+  mdrop = PK_NONE;
+  float thr = pk_threshold(tq[K - 1], live);
+  for (int c0 = K; c0 < cnt; c0 += 32) {
+    const int jl = c0 + lane;
+    const float bnd = jl < cnt ? key_lower_bound(s_a[jl], s_b[jl].x, s_e[jl], R) : F_INF;
+    unsigned m = __ballot_sync(FULL_MASK, !(bnd > thr));
+    auto take = [&](int pk) {
+      const bool better = pk < tq[K - 1];
+      int out = pk;
+      if (__any_sync(FULL_MASK, better)) {
+        int x = better ? pk : PK_NONE;
+        insert_pk<K>(tq, x);
+        out = better ? x : pk;
+      }
+      mdrop = min(mdrop, out);
+    };
+    while (m) {
+      const int j0 = c0 + __ffs(m) - 1;
+      m &= m - 1;
+      const bool two = m != 0;
+      const int j1 = two ? c0 + __ffs(m) - 1 : j0;
+      m &= m - 1;
+      const float4 a0 = s_a[j0], a1 = s_a[j1];
+      const float b0 = s_b[j0].x, b1 = s_b[j1].x;
+      const int p0 = pack_key(rank_key(px, py, a0.x, a0.y, a0.z, a0.w, b0), j0);
+      const int p1 = pack_key(rank_key(px, py, a1.x, a1.y, a1.z, a1.w, b1), j1);
+      take(p0);
+      if (two) take(p1);
+      // the threshold only falls: survivors are re-tested after every pair
+      thr = pk_threshold(tq[K - 1], live);
+      m &= __ballot_sync(FULL_MASK, !(bnd > thr));
+    }
+  }
+}
+
+// True when pass A's packed top K may differ from the exact (key, index) top
+// K at this pixel (see above).
+__device__ __forceinline__ bool pk_ambiguous(int tk, int mdrop) {
+  return tk < 0 || (tk != PK_NONE && (tk >> 8) == (mdrop >> 8));
+}
+
+// Exact selection for a warp with an ambiguous lane: the float pass A, the
+// tie cut-off, then every winner (q < tau, or q == tau and index <= the
+// cut-off) packed into tq, in ascending packed order.
+template <int K>
+__device__ __forceinline__ void exact_winners(const RenderParams& p, int cnt, float px,
+                                              float py, bool live, const float4& R,
+                                              const float4* s_a, const float2* s_b,
+                                              const float2* s_e, int (&tq)[K]) {
+  float tf[K];
+  float md;
+  culled_keys<K>(p, cnt, px, py, live, R, s_a, s_b, s_e, tf, md);
+  const float tau = tf[K - 1];
+  const bool tie = md == tau && tau < F_INF;
+  const int gcut =
+      __any_sync(FULL_MASK, tie) ? tie_cutoff<K>(cnt, px, py, tie, tau, tf, s_a, s_b) : GID_NONE;
+#pragma unroll
+  for (int k = 0; k < K; ++k) tq[k] = PK_NONE;
+  const float T = warp_max_key(live ? tau : 0.0f);
+  const int lane = threadIdx.x & 31;
+  for (int c0 = 0; c0 < cnt; c0 += 32) {
+    const int jl = c0 + lane;
+    const bool surv = jl < cnt && !(key_lower_bound(s_a[jl], s_b[jl].x, s_e[jl], R) > T);
+    unsigned m = __ballot_sync(FULL_MASK, surv);
+    while (m) {
+      const int j = c0 + __ffs(m) - 1;
+      m &= m - 1;
+      const float4 a = s_a[j];
+      const float2 b = s_b[j];
+      const float q = rank_key(px, py, a.x, a.y, a.z, a.w, b.x);
+      const bool win = q < tau || (q == tau && __float_as_int(b.y) <= gcut);
+      if (__any_sync(FULL_MASK, win)) {
+        int x = win ? pack_key(q, j) : PK_NONE;
+        insert_pk<K>(tq, x);
+      }
+    }
+  }
+}
+
+// Eq. 5 over the winners whose slots are in tq: their keys are recomputed
+// exactly, q_min is the smallest of them, and the winners are blended in the
+// packed order. all_valid: every entry of tq holds a winner (lists of at
+// least K entries).
+template <int K, int NC, int CH>
+__device__ __forceinline__ void blend_winners(const RenderParams& p, float px, float py,
+                                              const int (&tq)[K], bool all_valid,
+                                              const float4* s_a, const float2* s_b,
+                                              const float* s_col, PixelBlend<Chan<NC>::R>& r) {
+  constexpr int NCR = Chan<NC>::R;
+  const int n = nchan<NC>(p);
+  float qe[K];
+  float q0 = F_INF;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const bool ok = all_valid || tq[k] != PK_NONE;
+    const int j = ok ? (tq[k] & 0xff) : 0;
+    const float4 a = s_a[j];
+    qe[k] = ok ? rank_key(px, py, a.x, a.y, a.z, a.w, s_b[j].x) : F_INF;
+    q0 = fminf(q0, qe[k]);
+  }
+  r.q0 = p.normalize ? q0 : 0.0f;
+  r.Z = 0.0f;
+#pragma unroll
+  for (int c = 0; c < NCR; ++c) r.cr[c] = 0.0f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (all_valid || tq[k] != PK_NONE) {
+      const float w = blend_weight(r.q0, qe[k]);  // exactly 1 at q = q_min
+      r.Z += w;
+      float cc[NCR];
+      staged_colours<CH, NC>(p, s_col, s_b, tq[k] & 0xff, cc);
+#pragma unroll
+      for (int c = 0; c < NCR; ++c)
+        if (NC > 0 || c < n) r.cr[c] = fmaf(w, cc[c], r.cr[c]);
+    }
+  }
+  const float iz = p.normalize ? (r.Z > 0.0f ? 1.0f / r.Z : 0.0f) : 1.0f;
+#pragma unroll
+  for (int c = 0; c < NCR; ++c) r.cr[c] *= iz;
+  r.tau = F_INF;
+  r.gcut = GID_NONE;
+}
+
+// Records, for pass C, the winners of every live pixel of the warp. Each
+// pixel sets its bit in the warp's mask of every slot it won (cnt_w[slot],
+// zeroed before); then its k-th winner goes to wrec[k * NT] as (slot << 5 |
+// number of lower lanes that won the slot). The number of a slot's winning
+// pixels in the warp is the popcount of its mask. Returns the records made.
+template <int K, int NT>
+__device__ __forceinline__ int record_winners(const int (&tq)[K], bool live, unsigned* cnt_w,
+                                              unsigned short* wrec) {
+  const int lane = threadIdx.x & 31;
+  const unsigned bit = 1u << lane;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (live && tq[k] != PK_NONE) atomicOr(&cnt_w[tq[k] & 0xff], bit);
+  __syncwarp();
+  int nw = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (live && tq[k] != PK_NONE) {
+      const int j = tq[k] & 0xff;
+      wrec[k * NT] = (unsigned short)((j << 5) | __popc(cnt_w[j] & (bit - 1u)));
+      ++nw;
+    }
+  }
+  return nw;
+}
+
 template <int TILE, int K, int NC>
-__global__ void __launch_bounds__(TILE * TILE) k_render_fwd(RenderParams p) {
+__global__ void __launch_bounds__(TILE * TILE, TILE == 16 ? 6 : 16) k_render_fwd(RenderParams p) {
   constexpr int NT = TILE * TILE;
   __shared__ float4 s_a[NT];
   __shared__ float2 s_b[NT];
@@ -612,10 +842,19 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(RenderParams p) {
                          s_a, s_b, s_e, s_col, s_key);
     __syncthreads();
     const float4 R = block_rect<TILE>(x0, y0);
-    float mdrop;
-    culled_keys<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tq, mdrop);
-    culled_blend<K, NC, NT, NT, false>(p, len, px, py, in_img, R, tq, mdrop, s_a, s_b, s_e,
-                                       s_col, nullptr, nullptr, r);
+    if constexpr (K > 0) {
+      int tk[K];
+      int md;
+      packed_keys<K>(len, px, py, in_img, R, s_a, s_b, s_e, tk, md);
+      if (__any_sync(FULL_MASK, in_img && pk_ambiguous(tk[K - 1], md)))
+        exact_winners<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tk);
+      blend_winners<K, NC, NT>(p, px, py, tk, len >= K, s_a, s_b, s_col, r);
+    } else {
+      float mdrop;
+      culled_keys<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tq, mdrop);
+      culled_blend<K, NC, NT, NT, false>(p, len, px, py, in_img, R, tq, mdrop, s_a, s_b, s_e,
+                                         s_col, nullptr, nullptr, r);
+    }
   } else {
     select_keys<TILE, K, NT>(p, range, px, py, tq, s_a, s_b);
     blend_pass<TILE, K, NC, NT>(p, range, px, py, tq, r, s_a, s_b, s_col);
@@ -672,16 +911,15 @@ __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
 
 // Converts a candidate's moment sums into parameter gradients and adds them.
 // T = sum over its winning pixels of G*(dx, dy, dx^2, dx dy, dy^2) with
-// G = dL/dq; Tc = sum of w * (-g/(2Z)) per channel.
+// G = dL/dq; Tc = sum of w * (-g/(2Z)) per channel. The geometry comes from
+// the candidate's record: the conic (A00, B, A11), (t1, t2) and (cos, sin).
 template <int NC>
 __device__ __forceinline__ void emit_grad(const RenderParams& p, const TileCtx& t, int gid,
-                                          const float (&T)[5],
+                                          float A00, float B, float A11, float t1, float t2,
+                                          const float2& cs, const float (&T)[5],
                                           const float (&Tc)[Chan<NC>::R]) {
   constexpr int NCR = Chan<NC>::R;
   const int n = nchan<NC>(p);
-  const GRec rc = p.rec[gid];
-  const float2 cs = p.trig[gid];
-  const float A00 = rc.a.z, B = rc.a.w, A11 = rc.b.x, t1 = rc.b.z, t2 = rc.b.w;
   const float T1 = t1 * t1, T2 = t2 * t2;
   const float c2 = cs.x * cs.x, s2 = cs.y * cs.y, sc = cs.x * cs.y;
   // q = A00 dx^2 + B dx dy + A11 dy^2 with d = x - mu_px
@@ -792,7 +1030,7 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
 #pragma unroll
   for (int wb = 0; wb < NWB; ++wb) {
     pre[wb] = tot;
-    if (tid < cnt) tot += (int)s_cnt[wb * CH + tid];
+    if (tid < cnt) tot += __popc(s_cnt[wb * CH + tid]);
   }
   int P;
   const int base = block_scan_int(tid < cnt ? tot : 0, s_scan, P);  // ends every read of s_win
@@ -814,6 +1052,18 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
   }
   const int per = (P + NT - 1) / NT;  // pairs per thread
   const float inv_per = per > 0 ? 1.0f / (float)per : 0.0f;
+  // the epilogue's per-candidate geometry, requested now so that it arrives
+  // during the accumulation loop
+  int egid = -1;
+  float4 erb = make_float4(0.f, 0.f, 0.f, 0.f);
+  float2 ecs = make_float2(0.f, 0.f);
+  if (tid < cnt && s_coff[tid + 1] > s_coff[tid]) {
+    egid = __float_as_int(s_b[tid].y);
+    if ((unsigned)egid < (unsigned)p.N) {
+      erb = p.rec[egid].b;
+      ecs = p.trig[egid];
+    }
+  }
   __syncthreads();
 
   const int r0 = (int)threadIdx.x * per;
@@ -906,8 +1156,8 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
         for (int c = 0; c < NCR; ++c)
           if (NC > 0 || c < n) Tc[c] += s_slot_b[(5 + c) * NT + th];
       }
-      const int gid = __float_as_int(s_b[j].y);
-      if ((unsigned)gid < (unsigned)p.N) emit_grad<NC>(p, t, gid, T, Tc);
+      if ((unsigned)egid < (unsigned)p.N)
+        emit_grad<NC>(p, t, egid, s_a[j].z, s_a[j].w, erb.x, erb.z, erb.w, ecs, T, Tc);
     }
   }
 }
@@ -995,7 +1245,8 @@ __device__ __forceinline__ void chunked_pass_c(const RenderParams& p, const Tile
         for (int c = 0; c < NCR; ++c)
           if (NC > 0 || c < n) Tc[c] += src[5 + c];
       }
-      emit_grad<NC>(p, t, gid, T, Tc);
+      const GRec rc = p.rec[gid];
+      emit_grad<NC>(p, t, gid, rc.a.z, rc.a.w, rc.b.x, rc.b.z, rc.b.w, p.trig[gid], T, Tc);
     }
     __syncthreads();
   }
@@ -1050,11 +1301,22 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
                          (float)t.y0 + 0.5f * TILE, s_a, s_b, s_e, s_col, s_key);
     __syncthreads();
     const float4 R = block_rect<TILE>(t.x0, t.y0);
-    float mdrop;
-    culled_keys<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tq, mdrop);
-    culled_blend<K, NC, CH, NT, (K > 0)>(p, len, px, py, in_img, R, tq, mdrop, s_a, s_b, s_e,
-                                         s_col, s_cnt + (threadIdx.x >> 5) * CH,
-                                         s_win + threadIdx.x, r);
+    if constexpr (K > 0) {
+      unsigned* cnt_w = s_cnt + (threadIdx.x >> 5) * CH;  // this warp's winner masks
+      for (int j = threadIdx.x & 31; j < len; j += 32) cnt_w[j] = 0u;
+      int tk[K];
+      int md;
+      packed_keys<K>(len, px, py, in_img, R, s_a, s_b, s_e, tk, md);
+      if (__any_sync(FULL_MASK, in_img && pk_ambiguous(tk[K - 1], md)))
+        exact_winners<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tk);
+      blend_winners<K, NC, CH>(p, px, py, tk, len >= K, s_a, s_b, s_col, r);
+      r.nw = record_winners<K, NT>(tk, in_img, cnt_w, s_win + threadIdx.x);
+    } else {
+      float mdrop;
+      culled_keys<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tq, mdrop);
+      culled_blend<K, NC, CH, NT, false>(p, len, px, py, in_img, R, tq, mdrop, s_a, s_b, s_e,
+                                         s_col, nullptr, nullptr, r);
+    }
   } else {
     select_keys<TILE, K, CH>(p, t.range, px, py, tq, s_a, s_b);
     blend_pass<TILE, K, NC, CH>(p, t.range, px, py, tq, r, s_a, s_b, s_col);
@@ -1095,11 +1357,11 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
     if ((threadIdx.x & 31) == 0) s_loss[threadIdx.x >> 5] = l;
   }
   __syncthreads();
+  // the tile's loss is added after pass C, away from its barriers
+  float tile_loss = 0.0f;
   if (!p.grad_img && threadIdx.x == 0) {
-    float tot = 0.0f;
 #pragma unroll
-    for (int i = 0; i < NT / 32; ++i) tot += s_loss[i];
-    if (tot != 0.0f) atomicAdd(t.loss_acc, (double)tot);
+    for (int i = 0; i < NT / 32; ++i) tile_loss += s_loss[i];
   }
 
   // ---- pass C: candidate-major accumulation of the adjoint
@@ -1110,10 +1372,11 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   } else {
     chunked_pass_c<TILE, NC, CH>(p, t, s_ps0, s_ps1, s_gh, s_slot_a);
   }
+  if (tile_loss != 0.0f) atomicAdd(t.loss_acc, (double)tile_loss);
 }
 
 template <int TILE, int K, int NC>
-__global__ void __launch_bounds__(TILE * TILE) k_render_bwd(RenderParams p) {
+__global__ void __launch_bounds__(TILE * TILE, TILE == 16 ? 5 : 16) k_render_bwd(RenderParams p) {
   extern __shared__ __align__(16) float smem[];
   const int tile_id = blockIdx.x;
   TileCtx t;
@@ -1140,7 +1403,7 @@ __device__ __forceinline__ int image_of_tile(const BatchTables& bt, int tile) {
 // Persistent adjoint over the concatenated tiles of many images: each CTA
 // pulls tiles until none is left (no inter-CTA waits).
 template <int TILE, int K, int NC, int CH>
-__global__ void __launch_bounds__(TILE * TILE) k_render_bwd_batch(RenderParams p,
+__global__ void __launch_bounds__(TILE * TILE, 5) k_render_bwd_batch(RenderParams p,
                                                                   BatchTables bt) {
   extern __shared__ __align__(16) float smem[];
   __shared__ int s_item;

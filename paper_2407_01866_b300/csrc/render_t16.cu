@@ -15,14 +15,11 @@ template <int KK, int NCC>
 cudaError_t bwd_inst(const RenderParams& p, unsigned grid, cudaStream_t s) {
   const size_t bytes = sizeof(float) * (size_t)bwd_smem(16 * 16, NCC > 0 ? NCC : p.n, 16 * 16).total;
   if (bytes > 48 * 1024) {
-    static bool raised = false;  // idempotent; a repeated call is harmless
-    if (!raised) {
-      cudaError_t e = cudaFuncSetAttribute(k_render_bwd<16, KK, NCC>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)bytes);
-      if (e != cudaSuccess) return e;
-      raised = true;
-    }
+    // the limit is a per-device attribute of the kernel: set on every launch
+    // (idempotent, and right for whichever device and thread launches)
+    cudaError_t e = cudaFuncSetAttribute(k_render_bwd<16, KK, NCC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
   }
   k_render_bwd<16, KK, NCC><<<grid, 16 * 16, bytes, s>>>(p);
   return cudaGetLastError();
@@ -64,14 +61,11 @@ cudaError_t bwd_batch_inst(const RenderParams& p, const BatchTables& bt, int gri
                            cudaStream_t s) {
   const size_t bytes = sizeof(float) * (size_t)bwd_smem(16 * 16, NCC > 0 ? NCC : p.n, CH).total;
   if (bytes > 48 * 1024) {
-    static bool raised = false;  // idempotent; a repeated call is harmless
-    if (!raised) {
-      cudaError_t e = cudaFuncSetAttribute(k_render_bwd_batch<16, KK, NCC, CH>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)bytes);
-      if (e != cudaSuccess) return e;
-      raised = true;
-    }
+    // the limit is a per-device attribute of the kernel: set on every launch
+    // (idempotent, and right for whichever device and thread launches)
+    cudaError_t e = cudaFuncSetAttribute(k_render_bwd_batch<16, KK, NCC, CH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
   }
   k_render_bwd_batch<16, KK, NCC, CH><<<grid, 256, bytes, s>>>(p, bt);
   return cudaGetLastError();

@@ -8,7 +8,6 @@
 // igs_render_forward, but its scratch lives in one fixed-size array in this
 // file, which every GPU that loads the library holds until the process exits.
 #include <cstdio>
-#include <mutex>
 
 #include "imgs.h"
 #include "internal.h"
@@ -22,26 +21,18 @@ static __device__ __align__(256) unsigned char g_static_scratch[STATIC_SCRATCH_B
 
 namespace {
 
-constexpr int MAX_DEVICES = 64;
-std::mutex g_scratch_mutex;
-void* g_scratch_ptr[MAX_DEVICES] = {};
-
 // Device address of the scratch on the current device. In host code the
-// array's name is only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress, once per device, with that device current.
+// array's name is only a host-side stand-in, so the address comes from
+// cudaGetSymbolAddress with that device current. It is looked up on every
+// call (a cheap query next to a bin and render), so it stays right when the
+// device's context is torn down and created again (cudaDeviceReset) and the
+// module is loaded at another address. The first call on a device also loads
+// the module there.
 cudaError_t scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
+  *out = p;
   return cudaSuccess;
 }
 
@@ -65,9 +56,14 @@ extern "C" int igs_render_forward_static(const igs_gaussians* g, int32_t H, int3
     set_last_error(msg);
     return IGS_ERR_INVALID_ARG;
   }
-  // Room for the intersections: the largest capacity whose workspace fits.
+  // Room for the intersections: the largest capacity whose binning sections
+  // fit. A render needs only those (igs_preprocess_bin checks the same
+  // size); the fit-step images that igs_workspace_size adds for a config with
+  // an SSIM term are not used here.
+  igs_config bin_cfg = *cfg;
+  bin_cfg.ssim_weight = 0.0f;
   size_t fixed = 0;
-  if (int r = igs_workspace_size(g->N, g->n, H, W, cfg, 1, &fixed)) return r;
+  if (int r = igs_workspace_size(g->N, g->n, H, W, &bin_cfg, 1, &fixed)) return r;
   if (fixed > STATIC_SCRATCH_BYTES) {
     snprintf(msg, sizeof(msg),
              "igs_render_forward_static: N=%lld, n=%d, %dx%d needs %zu bytes before any "
@@ -80,7 +76,7 @@ extern "C" int igs_render_forward_static(const igs_gaussians* g, int32_t H, int3
   int64_t m_cap = (int64_t)((STATIC_SCRATCH_BYTES - fixed) / 8);
   size_t need = 0;
   while (m_cap > 1) {
-    if (int r = igs_workspace_size(g->N, g->n, H, W, cfg, m_cap, &need)) return r;
+    if (int r = igs_workspace_size(g->N, g->n, H, W, &bin_cfg, m_cap, &need)) return r;
     if (need <= STATIC_SCRATCH_BYTES) break;
     m_cap -= m_cap / 64 + 1;
   }

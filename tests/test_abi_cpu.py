@@ -11,14 +11,19 @@ from paper_2407_01866_b300 import lib as L
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_functions():
-    names = set()
-    for h in os.listdir(os.path.join(ROOT, "include")):
-        if h.endswith(".h"):
-            text = open(os.path.join(ROOT, "include", h)).read()
-            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-            names |= set(re.findall(r"^\s*(?:int|void)\s+(igs_\w+)\s*\(", text, flags=re.M))
-    return names
+# each public header and the library that exports its declarations
+HEADERS = {"imgs.h": "libimgs.so", "igs_peaks.h": "libigs_peaks.so"}
+
+
+def declared_functions(header="imgs.h"):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return set(re.findall(r"^\s*(?:int|void)\s+(igs_\w+)\s*\(", text, flags=re.M))
+
+
+def test_every_header_is_mapped_to_its_library():
+    assert sorted(h for h in os.listdir(os.path.join(ROOT, "include"))
+                  if h.endswith(".h")) == sorted(HEADERS)
 
 
 @pytest.fixture(scope="module")
@@ -42,6 +47,15 @@ def test_every_declared_symbol_is_exported_and_bound(lib):
     for name in names:
         assert hasattr(lib, name), f"{name} not exported by libimgs.so"
     assert names <= set(L.exported_names()), names - set(L.exported_names())
+
+
+def test_peak_probe_library_exports_its_header(lib):
+    from paper_2407_01866_b300 import peaks
+    names = declared_functions("igs_peaks.h")
+    assert names == {"igs_peak_probe"}
+    plib = peaks.load()
+    for name in names:
+        assert hasattr(plib, name), f"{name} not exported by libigs_peaks.so"
 
 
 def test_version_and_default_config(lib):

@@ -69,3 +69,41 @@ def test_static_scratch_rejects_oversized_problems():
     buf = ctypes.create_string_buffer(512)
     L.load().igs_last_error(buf, 512)
     assert b"static scratch" in buf.value
+
+
+def test_static_scratch_reports_too_many_intersections_then_recovers():
+    """Large Gaussians on a 1024x1024 image hit more tiles than the static
+    scratch's list holds: the GPU finds it out, the call returns
+    IGS_ERR_CAPACITY with an incomplete image, and the next, smaller call
+    still matches the workspace path."""
+    cfg = L.default_config()
+    H = W = 1024
+    n = 3
+    big = synth.gaussians(20000, n, seed=2, s_range=(50.0, 100.0))
+    ts = [torch.from_numpy(big[k]).cuda() for k in ("xy", "theta", "inv_scale", "color")]
+    img = torch.zeros((n, H, W), device="cuda")
+    with pytest.raises(L.IgsError) as e:
+        L.render_forward_static(L.gaussians_view(*ts), H, W, cfg, img)
+    assert e.value.code == L.IGS_ERR_CAPACITY
+    buf = ctypes.create_string_buffer(512)
+    L.load().igs_last_error(buf, 512)
+    assert b"static scratch" in buf.value
+    ts = _params(4096, n, 3)
+    img = torch.full((n, H, W), float("nan"), device="cuda")
+    L.render_forward_static(L.gaussians_view(*ts), H, W, cfg, img)
+    ref = _existing_path(ts, H, W, cfg)
+    torch.cuda.synchronize()
+    assert (img - ref).abs().max().item() <= PIX_TOL
+
+
+@pytest.mark.parametrize("H,W,n,tile,ssim", [(1024, 1024, 3, 16, 0.1), (200, 136, 9, 8, 0.0)])
+def test_static_scratch_other_shapes_match_workspace_render(H, W, n, tile, ssim):
+    """An SSIM weight in the config leaves the scratch to the binning (a
+    1024x1024 render fits), and a ragged 8x8-tile, 9-channel render matches."""
+    cfg = L.default_config(tile=tile, ssim_weight=ssim)
+    ts = _params(20000 if H == 1024 else 3000, n, 4)
+    img = torch.full((n, H, W), float("nan"), device="cuda")
+    L.render_forward_static(L.gaussians_view(*ts), H, W, cfg, img)
+    ref = _existing_path(ts, H, W, cfg)
+    torch.cuda.synchronize()
+    assert (img - ref).abs().max().item() <= PIX_TOL
