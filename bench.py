@@ -11,6 +11,7 @@ reported and `value` counts the steps of all ranks.
 """
 import argparse
 import json
+import multiprocessing
 import os
 import statistics
 import subprocess
@@ -35,11 +36,12 @@ UNIT = "fit steps/s"
 SM_COUNT = 148
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2032.0
-# DRAM bytes (read + write) of one fused forward + L1 + adjoint launch on the
-# fitted 2048^2 RGB state, from an ncu capture of that launch
-# (dram__bytes_read.sum 64.64 MB + dram__bytes_write.sum 1.69 MB); the
-# 2048^2 RGB workload only
-FUSED_TRAFFIC_2048_RGB = 66.33e6
+# DRAM bytes (read + write) of one fused forward + L1 + adjoint launch of the
+# current kernel on the 2048^2 RGB state the bench measures by default (20
+# steps from the initial parameters), from one ncu capture of that launch:
+# dram__bytes_read.sum 61,395,968 + dram__bytes_write.sum 872,448
+# (profiles/k_render_bwd_fit2048_rgb.md has the command)
+FUSED_TRAFFIC_2048_RGB = 62_268_416
 # library kernels of one fit step (the ncu launch list of the bench): finalize,
 # preprocess, 2 wide-Gaussian passes, 3 scan passes, emit, 2 segment sorts,
 # ranges, tile evaluations, fused adjoint, Adam
@@ -59,30 +61,65 @@ def fused_kernel_ops(evals, pixels, K, n):
     return evals * 8 + pixels * (K * (3 + n) + n + 3 * n + K * (32 + 3 * n))
 
 
-class ClockSampler:
-    """Samples nvidia-smi clocks and throttle reasons while running."""
+def fused_kernel_mufu(pixels, K):
+    """Algorithmic special-function operations of one fused launch: per pixel
+    K exponentials (the winners' weights) and one reciprocal (1/Z)."""
+    return pixels * (K + 1)
 
+
+class ClockSampler:
+    """Samples the SM clock and the throttle reasons while running: through
+    NVML (every 20 ms) where the library is present, else nvidia-smi (every
+    200 ms). Read-only queries."""
+
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
-        self.samples = []
+        self.samples = []   # (sm_mhz, sm_max_mhz, set of active reasons)
         self._stop = threading.Event()
         self._t = None
+        self._nvml = None
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self._h = pynvml.nvmlDeviceGetHandleByIndex(index)
+            self._nvml = pynvml
+            self._bits = {"hw_slowdown": pynvml.nvmlClocksEventReasonHwSlowdown,
+                          "hw_thermal_slowdown": pynvml.nvmlClocksEventReasonHwThermalSlowdown,
+                          "sw_thermal_slowdown": pynvml.nvmlClocksEventReasonSwThermalSlowdown,
+                          "sw_power_cap": pynvml.nvmlClocksEventReasonSwPowerCap}
+        except Exception:
+            self._nvml = None
+
+    def _sample_nvml(self):
+        n = self._nvml
+        sm = float(n.nvmlDeviceGetClockInfo(self._h, n.NVML_CLOCK_SM))
+        mx = float(n.nvmlDeviceGetMaxClockInfo(self._h, n.NVML_CLOCK_SM))
+        r = n.nvmlDeviceGetCurrentClocksEventReasons(self._h)
+        self.samples.append((sm, mx, {k for k, b in self._bits.items() if r & b}))
+
+    def _sample_smi(self):
+        out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                              "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=5).stdout.strip()
+        if out:
+            f = [x.strip() for x in out.split(",")]
+            sm = float(f[0]) if f[0].replace(".", "").isdigit() else None
+            mx = float(f[1]) if f[1].replace(".", "").isdigit() else None
+            self.samples.append((sm, mx, {self.REASONS[i] for i in range(4)
+                                          if len(f) > 3 + i and f[3 + i].lower() == "active"}))
 
     def _run(self):
         while not self._stop.is_set():
             try:
-                out = subprocess.run(["nvidia-smi", "-i", str(self.index),
-                                      f"--query-gpu={self.Q}", "--format=csv,noheader,nounits"],
-                                     capture_output=True, text=True, timeout=5).stdout.strip()
-                if out:
-                    self.samples.append([x.strip() for x in out.split(",")])
+                self._sample_nvml() if self._nvml else self._sample_smi()
             except Exception:
                 pass
-            self._stop.wait(0.2)
+            self._stop.wait(0.02 if self._nvml else 0.2)
 
     def __enter__(self):
         self._t = threading.Thread(target=self._run, daemon=True)
@@ -94,16 +131,14 @@ class ClockSampler:
         self._t.join(timeout=10)
 
     def summary(self):
-        if not self.samples:
+        sm = [x[0] for x in self.samples if x[0] is not None]
+        mx = [x[1] for x in self.samples if x[1] is not None]
+        if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4)
-                          if len(s) > 3 + i and s[3 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.samples)}
+        reasons = sorted(set().union(*[x[2] for x in self.samples]))
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples),
+                "via": "nvml" if self._nvml else "nvidia-smi"}
 
 
 def rank_env():
@@ -146,30 +181,73 @@ def make_inputs(w=WORKLOAD):
     return target, synth.packed(d)
 
 
-def cpu_baseline(target, P, budget_s=15.0, seed=0, w=WORKLOAD):
-    """Oracle fit step (forward + L1 + adjoint over sampled pixels), extrapolated."""
+def host_cores():
+    """(cores this process may run on, os.cpu_count())."""
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except AttributeError:
+        usable = os.cpu_count() or 1
+    return usable, os.cpu_count()
+
+
+def _oracle_worker(job):
+    """One oracle process: forward + L1 sign + adjoint, 16 pixels at a time,
+    over pixels[start::stride] until the deadline. Returns pixels done."""
+    P, target_sample, pix, H, W, n, start, stride, deadline = job
     from oracle import image_gs as O
-    from paper_2407_01866_b300 import synth
-    H, W, n = w["H"], w["W"], w["n"]
     g = O.Gaussians.from_packed(P)
-    pix = synth.sample_pixels(4096, H, W, seed=seed)
     done = 0
-    t0 = time.perf_counter()
-    while done < len(pix) and time.perf_counter() - t0 < budget_s:
-        chunk = pix[done:done + 16]
+    mine = pix[start::stride]
+    tgt = target_sample[start::stride]
+    for c0 in range(0, len(mine), 16):
+        if time.time() > deadline:
+            break
+        chunk = mine[c0:c0 + 16]
         pts = O.pixel_centres(chunk)
         img = O.render_points(g, pts, H, W)
-        tgt = target[:, chunk[:, 0], chunk[:, 1]].T
-        go = np.sign(img - tgt) / (H * W * n)
+        go = np.sign(img - tgt[c0:c0 + 16]) / (H * W * n)
         O.backward_points(g, pts, go, H, W)
         done += len(chunk)
-    dt = time.perf_counter() - t0
-    per_pixel = dt / done
-    step_s = per_pixel * H * W
-    return {"value": 1.0 / step_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} random pixels of the {H}x{W} workload, forward + L1 + adjoint "
-                      f"brute force in float64 over all {w['N']} Gaussians ({dt:.1f} s), "
-                      "extrapolated to the full frame"}
+    return done
+
+
+def cpu_baseline(target, P, budget_s=15.0, seed=0, w=WORKLOAD):
+    """The oracle's fit step (forward + L1 + adjoint, float64 brute force over
+    all N Gaussians per pixel) on random pixels of the workload, one process
+    per usable host core for about budget_s seconds, extrapolated to the
+    frame."""
+    from paper_2407_01866_b300 import synth
+    H, W, n = w["H"], w["W"], w["n"]
+    usable, total = host_cores()
+    pix = synth.sample_pixels(64 * usable + 4096, H, W, seed=seed)
+    tsample = target[:, pix[:, 0], pix[:, 1]].T.copy()
+    # one thread per process: the processes are the parallelism
+    env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                                "MKL_NUM_THREADS")}
+    for k in env_keep:
+        os.environ[k] = "1"
+    try:
+        ctx = multiprocessing.get_context("spawn")   # never fork a CUDA process
+        with ctx.Pool(usable) as pool:
+            pool.map(_oracle_worker, [(P, tsample[:16], pix[:16], H, W, n, 0, 1,
+                                       time.time() + 60.0)] * usable)   # imports, warm-up
+            t0 = time.time()
+            jobs = [(P, tsample, pix, H, W, n, r, usable, t0 + budget_s) for r in range(usable)]
+            done = sum(pool.map(_oracle_worker, jobs))
+            dt = time.time() - t0
+    finally:
+        for k, v in env_keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    step_s = dt / max(done, 1) * H * W
+    return {"value": 1.0 / step_s, "unit": UNIT, "cores": usable, "kind": "oracle",
+            "host_cpu_count": total,
+            "sample": f"{done} random pixels of the {H}x{W} workload in {dt:.1f} s on {usable} "
+                      f"processes (affinity mask of {usable} of {total} host cores), "
+                      f"forward + L1 + adjoint brute force in float64 over all {w['N']} "
+                      "Gaussians, extrapolated to the full frame"}
 
 
 def run_reference(args):
@@ -179,7 +257,7 @@ def run_reference(args):
     target, P = make_inputs()
     times = []
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(target, P, budget_s=max(5.0, 60.0 / max(1, args.steps + args.warmup)),
+        cb = cpu_baseline(target, P, budget_s=max(2.0, 60.0 / max(1, args.steps + args.warmup)),
                           seed=i)
         if i >= args.warmup:
             times.append(1.0 / cb["value"])
@@ -191,8 +269,8 @@ def run_reference(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD["name"], "H": 2048, "W": 2048, "n": 3,
                        "N": 100_000, "K": 10, "tile": 16},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": cb["sample"]},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                             "host_cpu_count": cb["host_cpu_count"], "sample": cb["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -220,6 +298,18 @@ def run_ours(args, w=WORKLOAD):
     st0 = L.read_stats(bins0)
     cap = int(st0.m_needed * 3) + 4096
     ws = L.alloc_workspace(L.workspace_size(N, n, H, W, cfg, cap), dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
+
+    # the dominant kernel (fused forward + L1 + adjoint) on the initial parameters
+    evals_init = int(st0.evals)
+    k_ms_init = None
+    if not args.kernel_once:
+        G0 = torch.zeros_like(P0)
+        view0 = L.packed_view(P0, n)
+        k_ms_init = _time_events(lambda: L.render_backward(view0, bins0, cfg, None, target, G0),
+                                 20, flush, warmup=3)
+        del G0
+    del binner, bins0
 
     P = P0.clone()
     G = torch.zeros_like(P)
@@ -251,7 +341,6 @@ def run_ours(args, w=WORKLOAD):
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
         step_fn()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
 
     if args.kernel_once:
         # the fit (graph replays, as timed below), then one binning, one forward
@@ -283,36 +372,35 @@ def run_ours(args, w=WORKLOAD):
             graph.replay()
             ends[i].record()
         torch.cuda.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    ms = float(statistics.mean(step_ms))
-    ms = max_over_ranks(ms, dist, dev)
-    if dist:
-        dist.barrier()
+        step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        ms = float(statistics.mean(step_ms))
+        ms = max_over_ranks(ms, dist, dev)
+        if dist:
+            dist.barrier()
 
-    # binning statistics of the final state (evals of one forward)
-    stats = L.read_stats(L.preprocess_bin(L.packed_view(P, n), H, W, cfg, ws, cap))
-    if stats.flags & L.FLAG_CAPACITY:
-        raise RuntimeError("intersection capacity exceeded during the benchmark")
-    evals = int(stats.evals)
-    pixels = H * W
+        # binning statistics of the final state (evals of one forward)
+        stats = L.read_stats(L.preprocess_bin(L.packed_view(P, n), H, W, cfg, ws, cap))
+        if stats.flags & L.FLAG_CAPACITY:
+            raise RuntimeError("intersection capacity exceeded during the benchmark")
+        evals = int(stats.evals)
+        pixels = H * W
 
-    # ---- dominant kernel (fused forward + L1 + adjoint), timed alone ----
-    bins = L.preprocess_bin(L.packed_view(P, n), H, W, cfg, ws, cap)
-    view = L.packed_view(P, n)
-    kstart = [torch.cuda.Event(enable_timing=True) for _ in range(20)]
-    kend = [torch.cuda.Event(enable_timing=True) for _ in range(20)]
-    for i in range(23):
-        flush.fill_(i & 0xff)
-        if i >= 3:
-            kstart[i - 3].record()
-        L.render_backward(view, bins, cfg, None, target, G)
-        if i >= 3:
-            kend[i - 3].record()
-    torch.cuda.synchronize()
-    k_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(kstart, kend))
+        # ---- dominant kernel (fused forward + L1 + adjoint), timed alone on
+        # the final state, on the stream it is launched on ----
+        bins = L.preprocess_bin(L.packed_view(P, n), H, W, cfg, ws, cap)
+        view = L.packed_view(P, n)
+        k_ms = _time_events(lambda: L.render_backward(view, bins, cfg, None, target, G), 20,
+                            flush, warmup=3)
+
+        # ---- measured peaks of this GPU: FP32 FMA lanes and the exp2 unit ----
+        from paper_2407_01866_b300 import peaks
+        fp32_peak = max(peaks.probe("ffma", iters=2000, reps=5)[0],
+                        peaks.probe("ffma2", iters=1000, reps=5)[0])
+        mufu_peak = peaks.probe("ex2", iters=500, reps=5)[0]
     ops = fused_kernel_ops(evals, pixels, cfg.K, n)
-    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
     achieved = ops / (k_ms * 1e-3)
+    mufu_ops = fused_kernel_mufu(pixels, cfg.K)
+    ops_init = fused_kernel_ops(evals_init, pixels, cfg.K, n)
 
     # ---- end to end through the C ABI with host buffers ----
     # Every step copies its target from pinned host memory and reads its loss
@@ -376,14 +464,26 @@ def run_ours(args, w=WORKLOAD):
             "final_loss": float(loss.item()),
             "gpu_launches": (KERNELS_PER_FIT_STEP + (0 if half is None else 2)
                              + (SSIM_EXTRA_KERNELS if args.ssim > 0 else 0)) * args.steps,
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-                         "unit": "T fp32 lane-ops/s", "frac": achieved / peak,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak / 1e12,
+                         "unit": "T fp32 lane-ops/s", "frac": achieved / fp32_peak,
                          "traffic": (FUSED_TRAFFIC_2048_RGB
                                      if w["name"] == "fit2048_rgb" and half is None else None),
                          "traffic_unit": "bytes per launch",
                          "kernel": "k_render_bwd (fused forward + L1 + adjoint)",
-                         "kernel_ms": k_ms,
-                         "peak_note": "148 SMs x 128 FP32 lanes x 2032 MHz (max SM clock)"},
+                         "kernel_ms": k_ms, "ops_per_launch": ops,
+                         "peak_note": "measured on this GPU in this run (libigs_peaks: chains of "
+                                      "fma.rn.f32 and fma.rn.f32x2 over every SM, the faster "
+                                      "lane rate), under the clocks reported below; "
+                                      f"nominal {SM_COUNT} SMs x {FP32_LANES_PER_SM} lanes x "
+                                      f"{SM_MAX_MHZ:.0f} MHz = "
+                                      f"{SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ / 1e6:.1f} T",
+                         "mufu": {"ops_per_launch": mufu_ops, "peak": mufu_peak / 1e12,
+                                  "unit": "T ex2/s (measured)",
+                                  "frac": mufu_ops / (k_ms * 1e-3) / mufu_peak},
+                         "initial_state": {"kernel_ms": k_ms_init, "evals": evals_init,
+                                           "ops_per_launch": ops_init,
+                                           "achieved": ops_init / (k_ms_init * 1e-3) / 1e12,
+                                           "frac": ops_init / (k_ms_init * 1e-3) / fp32_peak}},
             "e2e": {"value": world * 1000.0 / e2e_ms, "unit": UNIT,
                     "h2d_bytes_per_step": int(target.numel() * 4), "d2h_bytes_per_step": 4},
             "clocks": clocks.summary(),
@@ -395,9 +495,14 @@ def run_ours(args, w=WORKLOAD):
         dist.destroy_process_group()
 
 
-def _time_events(fn, steps, flush=None):
-    """Mean ms of fn() over `steps` runs, CUDA events on the current stream."""
+def _time_events(fn, steps, flush=None, warmup=0):
+    """Mean ms of fn() over `steps` runs (after `warmup` untimed ones), CUDA
+    events on the current stream, L2 flushed before each run if given."""
     import torch
+    for i in range(warmup):
+        if flush is not None:
+            flush.fill_(i & 0xff)
+        fn()
     st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     for i in range(steps):
