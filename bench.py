@@ -658,7 +658,13 @@ def run_decode(args):
             "dtype": "f32 math, f16/bf16/f32 storage", "data": "synthetic",
             "config": {"workload": "decode8192", "H": H, "W": W, "n": n, "N": N, "queries": Q,
                        "l2": "flushed between timed launches (256 MB write)"},
-            "by_storage": res, "clocks": clocks.summary()}
+            "by_storage": res,
+            "half_vs_f32": {k: {"decode_speedup": res["f32"]["decode_ms"] / res[k]["decode_ms"],
+                                "render_speedup": res["f32"]["render_ms"] / res[k]["render_ms"],
+                                "render_evals_per_s_ratio": res[k]["render_evals_per_s"]
+                                / res["f32"]["render_evals_per_s"]}
+                            for k in ("f16", "bf16")},
+            "clocks": clocks.summary()}
     print(json.dumps(line))
 
 

@@ -107,7 +107,8 @@ typedef struct {
   /* weight w of the SSIM term of the fit loss L1 + w L_SSIM (Sec. 4.1:
    * 0.1). 0 (default) fits against L1 alone with the fused adjoint; w > 0
    * runs forward render, igs_image_loss and the adjoint with that upstream
-   * gradient, and needs the larger workspace igs_workspace_size reports */
+   * gradient (single image and batched form), and needs the larger
+   * workspace igs_workspace_size / igs_batch_workspace_size report */
   float ssim_weight;
 } igs_config;
 
@@ -135,6 +136,12 @@ typedef struct {
   const float* trig;          /* [N][2] (cos, sin) (internal) */
   const float* color;         /* [N][n] float32 colours (internal) */
   void* status;               /* device status block (internal) */
+  int32_t dtype;              /* storage of the binned parameters (IGS_F32...) */
+  const void* rec16;          /* F16/BF16 storage: [N] 16-byte records of the
+                                 stored mu bits and the binary32 conic, read
+                                 by the render and decode loops (internal) */
+  const void* color16;        /* F16/BF16 storage: [N][n] stored colour bits
+                                 (internal); both NULL for F32 */
 } igs_bins;
 
 /* Library version: major*10000 + minor*100 + patch. */
@@ -275,13 +282,39 @@ int igs_batch_setup(const igs_batch_shape* shape, const igs_config* cfg, void* w
 /* One optimisation step of every image of the batch (Sec. 3.3, Sec. 4.1,
  * as igs_fit_step): batched preprocess/bin over the concatenated tile
  * space, one persistent fused forward + L1 + adjoint launch over all tiles,
- * Adam, clamps. Stream-ordered, no host synchronisation, graph-capturable
- * after igs_batch_setup. tuning may be NULL (defaults). d_loss_out
- * (nullable, device float [B]) receives each image's mean L1 loss. */
+ * Adam, clamps. With cfg->ssim_weight > 0 (Sec. 4.1: L1 + 0.1 L_SSIM) the
+ * step renders every image (igs_render_forward_batch), evaluates each
+ * image's loss and image-space gradient (as igs_image_loss) and runs the
+ * persistent adjoint on that gradient; the workspace is larger (see
+ * igs_batch_workspace_size). Stream-ordered, no host synchronisation,
+ * graph-capturable after igs_batch_setup. tuning may be NULL (defaults).
+ * d_loss_out (nullable, device float [B]) receives each image's mean loss
+ * (L1, plus w (1 - SSIM) with the SSIM term). */
 int igs_fit_batch_step(const igs_fit_state* st, const float* d_targets,
                        const igs_batch_shape* shape, const igs_config* cfg,
                        const igs_batch_tuning* tuning, void* ws, size_t ws_bytes,
                        int64_t m_capacity, float* d_loss_out, igs_stream stream);
+
+/* Forward render (Eq. 5, Sec. 3.2) of every image of the batch into
+ * d_imgs, the images' planar [n][H_b][W_b] float32 arrays concatenated in
+ * image order. d_params [N][5+n] (N = sum N_b, 16-byte aligned) are the
+ * concatenated packed rows. Bins the batch into the workspace (after
+ * igs_batch_setup), then renders every tile of every image in one launch.
+ * Stream-ordered, no host synchronisation. */
+int igs_render_forward_batch(const float* d_params, int64_t N, const igs_batch_shape* shape,
+                             const igs_config* cfg, void* ws, size_t ws_bytes,
+                             int64_t m_capacity, float* d_imgs, igs_stream stream);
+
+/* Adjoint (Sec. 3.3: gradients through the K retained Gaussians) of every
+ * image of the batch for an external upstream gradient d_grad_imgs (the
+ * images' dL/dc_r, laid out like d_imgs of igs_render_forward_batch), with
+ * the persistent mapping `tuning` (NULL: defaults). d_grad [N][5+n]
+ * (16-byte aligned) is overwritten with dL/dp in the packed order. Bins the
+ * batch into the workspace first. Stream-ordered, no host synchronisation. */
+int igs_render_backward_batch(const float* d_params, int64_t N, const float* d_grad_imgs,
+                              const igs_batch_shape* shape, const igs_config* cfg,
+                              const igs_batch_tuning* tuning, void* ws, size_t ws_bytes,
+                              int64_t m_capacity, float* d_grad, igs_stream stream);
 
 /* Chooses the persistent adjoint's mapping for this batch by timing every
  * candidate (CTAs per SM x stage x order) on the current parameters: bins

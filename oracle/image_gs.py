@@ -310,6 +310,35 @@ def selection(g, pts, H, W, K=10, tile=16):
     return res
 
 
+def selection_f64(g, pts, H, W, K=10, tile=16):
+    """Per point, the indices the top-K of Sec. 3.2 keeps when it ranks by
+    float64 keys (quad_form64, the binary32 rounding of the key evaluation
+    removed; ties to the smaller index) instead of the binary32 keys. The
+    candidates are the same S_j. List of index arrays, ranked."""
+    pts = np.asarray(pts, dtype=F64).reshape(-1, 2)
+    res = []
+    for x, y in pts:
+        tx, ty = _tile_of(x, y, tile, H, W)
+        member = np.nonzero(tile_members(g, tx, ty, tile, H, W))[0]
+        if member.size == 0:
+            res.append(member)
+            continue
+        q64 = quad_form64(np.array([[x]]), np.array([[y]]), g, H, W, idx=member[None, :])
+        cols = _select_topk(q64, member, K)
+        res.append(member[cols[0]])
+    return res
+
+
+def selection_mismatches(g, pts, H, W, K=10, tile=16):
+    """Points whose selected set under binary32 keys (the decision the kernels
+    take) differs from the set under float64 keys: the pixels where rounding
+    of the key decides which Gaussians are kept (near-ties at the K-th place).
+    Returns the indices of those points."""
+    a = selection(g, pts, H, W, K, tile)
+    b = selection_f64(g, pts, H, W, K, tile)
+    return [i for i, (u, v) in enumerate(zip(a, b)) if set(u.tolist()) != set(v.tolist())]
+
+
 # ---------------------------------------------------------------------------
 # Adjoint: gradients through the K retained Gaussians (Sec. 3.3).
 # ---------------------------------------------------------------------------

@@ -59,6 +59,8 @@ WsLayout ws_layout_tiles(int64_t N, int n, int64_t T, int64_t m_cap) {
   L.rec = take(sizeof(GRec) * (size_t)N);
   L.trig = take(sizeof(float2) * (size_t)N);
   L.color = take(sizeof(float) * (size_t)N * n);
+  L.rec16 = take(sizeof(HRec) * (size_t)N);
+  L.col16 = take(sizeof(unsigned short) * (size_t)N * n);
   L.tcnt = take(sizeof(unsigned int) * (size_t)T);
   L.toff = take(sizeof(unsigned long long) * (size_t)T);
   L.part = take(sizeof(unsigned long long) * (size_t)L.part_len);
@@ -129,6 +131,11 @@ static RenderParams render_params(const igs_bins* b) {
   p.tile = b->tile;
   p.status = static_cast<DevStatus*>(b->status);
   p.inv_count = (float)(1.0 / ((double)b->H * b->W * b->n));
+  if ((b->dtype == IGS_F16 || b->dtype == IGS_BF16) && b->rec16 && b->color16) {
+    p.rec16 = static_cast<const HRec*>(b->rec16);
+    p.col16 = static_cast<const unsigned short*>(b->color16);
+    p.hdt = b->dtype == IGS_F16 ? 1 : 2;
+  }
   return p;
 }
 
@@ -258,6 +265,10 @@ int igs_preprocess_bin(const igs_gaussians* g, int32_t H, int32_t W, const igs_c
   p.rec = reinterpret_cast<GRec*>(base + L.rec);
   p.trig = reinterpret_cast<float2*>(base + L.trig);
   p.color_out = reinterpret_cast<float*>(base + L.color);
+  if (g->dtype != IGS_F32) {
+    p.rec16 = reinterpret_cast<HRec*>(base + L.rec16);
+    p.col16 = reinterpret_cast<unsigned short*>(base + L.col16);
+  }
   p.tcnt = reinterpret_cast<unsigned int*>(base + L.tcnt);
   p.toff = reinterpret_cast<unsigned long long*>(base + L.toff);
   p.vals = reinterpret_cast<unsigned int*>(base + L.vals);
@@ -287,6 +298,9 @@ int igs_preprocess_bin(const igs_gaussians* g, int32_t H, int32_t W, const igs_c
   out->trig = reinterpret_cast<const float*>(p.trig);
   out->color = p.color_out;
   out->status = status;
+  out->dtype = g->dtype;
+  out->rec16 = p.rec16;
+  out->color16 = p.col16;
   return IGS_OK;
 }
 

@@ -9,6 +9,12 @@
 // counter, which balances small and large images on the 148 SMs; Adam runs
 // once over all parameters. The per-image tables live in the workspace after
 // the single-image sections and are written once by igs_batch_setup.
+//
+// With the SSIM term (Sec. 4.1: L1 + 0.1 L_SSIM) a step renders every image
+// (one launch over all tiles), evaluates each image's loss and its image-space
+// gradient, and runs the persistent adjoint on that gradient. The batched
+// forward and the adjoint of an external upstream gradient are also entry
+// points of their own.
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
@@ -28,8 +34,11 @@ constexpr int BATCH_MIN_STAGE = 64;  // smallest one-stage list of the batched a
 struct BatchGeom {
   WsLayout L;
   size_t dims, tile_off, pix_off, gauss_off, img_of, loss, work, total;
-  int64_t Ntot, T;
-  int B, n;
+  // SSIM fits only (0 otherwise): renderings, their loss gradients, and the
+  // image-loss scratch of the largest image
+  size_t img, gimg, loss_scratch;
+  int64_t Ntot, T, pixels;
+  int B, n, Hmax, Wmax;
 };
 
 int bfail(int code, const char* fmt, ...) {
@@ -45,9 +54,9 @@ int bfail(int code, const char* fmt, ...) {
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
 int batch_geom(const igs_batch_shape* sh, const igs_config* cfg, int64_t m_cap, BatchGeom* G) {
-  if (cfg && cfg->ssim_weight > 0.0f)
-    return bfail(IGS_ERR_INVALID_ARG, "batch: the SSIM term is not supported (L1 only)");
   if (!sh || !cfg) return bfail(IGS_ERR_INVALID_ARG, "batch: NULL shape or config");
+  if (!(cfg->ssim_weight >= 0.0f && cfg->ssim_weight <= 1e6f))
+    return bfail(IGS_ERR_INVALID_ARG, "batch: ssim_weight must be finite and >= 0");
   if (sh->B < 1 || !sh->H || !sh->W || !sh->N)
     return bfail(IGS_ERR_INVALID_ARG, "batch: B < 1 or a NULL size array");
   if (sh->n < 1 || sh->n > 32) return bfail(IGS_ERR_INVALID_ARG, "batch: n = %d", sh->n);
@@ -57,7 +66,8 @@ int batch_geom(const igs_batch_shape* sh, const igs_config* cfg, int64_t m_cap, 
     return bfail(IGS_ERR_INVALID_ARG, "batch: unsupported K=%d", cfg->K);
   if (m_cap < 1 || m_cap > (int64_t)INT32_MAX)
     return bfail(IGS_ERR_INVALID_ARG, "batch: m_capacity out of range");
-  int64_t N = 0, T = 0;
+  int64_t N = 0, T = 0, pixels = 0;
+  int Hmax = 0, Wmax = 0;
   for (int b = 0; b < sh->B; ++b) {
     const int H = sh->H[b], W = sh->W[b];
     if (H <= 0 || W <= 0 || H > (1 << 20) || W > (1 << 20) || sh->N[b] < 0)
@@ -65,6 +75,9 @@ int batch_geom(const igs_batch_shape* sh, const igs_config* cfg, int64_t m_cap, 
                    (long long)sh->N[b]);
     N += sh->N[b];
     T += (int64_t)((W + BATCH_TILE - 1) / BATCH_TILE) * ((H + BATCH_TILE - 1) / BATCH_TILE);
+    pixels += (int64_t)H * W;
+    Hmax = std::max(Hmax, H);
+    Wmax = std::max(Wmax, W);
   }
   if (N > (int64_t)INT32_MAX || T > (int64_t)INT32_MAX)
     return bfail(IGS_ERR_INVALID_ARG, "batch: too many Gaussians or tiles");
@@ -78,11 +91,21 @@ int batch_geom(const igs_batch_shape* sh, const igs_config* cfg, int64_t m_cap, 
   G->img_of = o;    o = up256(o + sizeof(int) * (size_t)N);
   G->loss = o;      o = up256(o + sizeof(double) * B);
   G->work = o;      o = up256(o + sizeof(unsigned int));
+  G->img = G->gimg = G->loss_scratch = 0;
+  if (cfg->ssim_weight > 0.0f) {
+    const size_t img_bytes = sizeof(float) * (size_t)sh->n * (size_t)pixels;
+    G->img = o;          o = up256(o + img_bytes);
+    G->gimg = o;         o = up256(o + img_bytes);
+    G->loss_scratch = o; o = up256(o + image_loss_scratch_bytes(sh->n, Hmax, Wmax));
+  }
   G->total = o;
   G->Ntot = N;
   G->T = T;
+  G->pixels = pixels;
   G->B = B;
   G->n = sh->n;
+  G->Hmax = Hmax;
+  G->Wmax = Wmax;
   return IGS_OK;
 }
 
@@ -117,7 +140,7 @@ BatchTables tables(const BatchGeom& G, char* base, int order) {
 // Bins the concatenated Gaussians of the fit state; returns render params.
 // Lists longer than sort_min (the smallest stage the adjoint will run with)
 // are sorted by Gaussian index; shorter ones are ranked by the renderer.
-int batch_bin(const igs_fit_state* st, const BatchGeom& G, const igs_config* cfg, char* base,
+int batch_bin(const float* params, const BatchGeom& G, const igs_config* cfg, char* base,
               int64_t m_cap, int sort_min, RenderParams* rp, cudaStream_t s) {
   const WsLayout& L = G.L;
   DevStatus* status = reinterpret_cast<DevStatus*>(base + L.status);
@@ -125,10 +148,10 @@ int batch_bin(const igs_fit_state* st, const BatchGeom& G, const igs_config* cfg
   const int np = 5 + G.n;
   PrepParams p;
   memset(&p, 0, sizeof(p));
-  p.xy = st->params;
-  p.theta = st->params + 2;
-  p.inv_scale = st->params + 3;
-  p.color = st->params + 5;
+  p.xy = params;
+  p.theta = params + 2;
+  p.inv_scale = params + 3;
+  p.color = params + 5;
   p.xy_stride = p.theta_stride = p.inv_scale_stride = p.color_stride = np;
   p.N = G.Ntot;
   p.n = G.n;
@@ -183,15 +206,19 @@ int check_tuning(const igs_batch_tuning& t) {
 }
 
 // Adjoint of every image: zero grad and per-image sums, one persistent launch.
-int batch_adjoint(const igs_fit_state* st, const float* d_targets, const BatchGeom& G,
-                  const igs_config* cfg, const igs_batch_tuning& tn, char* base,
-                  RenderParams rp, cudaStream_t s) {
-  BCUDA(cudaMemsetAsync(st->grad, 0, sizeof(float) * (size_t)G.Ntot * (5 + G.n), s),
+// With d_targets the upstream gradient is the fused L1 one; otherwise
+// d_grad_imgs (concatenated planar images) is the upstream gradient.
+int batch_adjoint(float* grad, const float* d_targets, const float* d_grad_imgs,
+                  const BatchGeom& G, const igs_config* cfg, const igs_batch_tuning& tn,
+                  char* base, RenderParams rp, cudaStream_t s) {
+  BCUDA(cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)G.Ntot * (5 + G.n), s),
         "batch: zero grad");
-  BCUDA(cudaMemsetAsync(base + G.loss, 0, sizeof(double) * G.B, s), "batch: zero losses");
+  if (d_targets)
+    BCUDA(cudaMemsetAsync(base + G.loss, 0, sizeof(double) * G.B, s), "batch: zero losses");
   BCUDA(cudaMemsetAsync(base + G.work, 0, sizeof(unsigned int), s), "batch: zero counter");
   rp.target = d_targets;
-  rp.grad = st->grad;
+  rp.grad_img = d_grad_imgs;
+  rp.grad = grad;
   rp.normalize = cfg->normalize;
   const BatchTables bt = tables(G, base, tn.order);
   BCUDA(launch_render_bwd_batch(rp, bt, cfg->K, tn.stage, tn.ctas_per_sm * sm_count(), s),
@@ -211,11 +238,91 @@ int check_state(const igs_fit_state* st, const BatchGeom& G, const float* d_targ
   return IGS_OK;
 }
 
+// Forward render of every image into the concatenated planar images d_imgs.
+int batch_forward(const BatchGeom& G, const igs_config* cfg, char* base, RenderParams rp,
+                  float* d_imgs, cudaStream_t s) {
+  rp.img = d_imgs;
+  rp.normalize = cfg->normalize;
+  const BatchTables bt = tables(G, base, 0);
+  BCUDA(launch_render_fwd_batch(rp, bt, cfg->K, s), "batch: forward");
+  return IGS_OK;
+}
+
+// L1 + w (1 - SSIM) of every rendering against its target: the image-space
+// gradients into gimg, the per-image loss sums into the batch's loss table.
+int batch_image_loss(const BatchGeom& G, const igs_batch_shape* sh, const igs_config* cfg,
+                     const float* d_targets, char* base, cudaStream_t s) {
+  BCUDA(cudaMemsetAsync(base + G.loss, 0, sizeof(double) * G.B, s), "batch: zero losses");
+  const float* img = reinterpret_cast<const float*>(base + G.img);
+  float* gimg = reinterpret_cast<float*>(base + G.gimg);
+  double* loss = reinterpret_cast<double*>(base + G.loss);
+  int64_t off = 0;
+  for (int b = 0; b < G.B; ++b) {
+    const int H = sh->H[b], W = sh->W[b];
+    BCUDA(launch_image_loss(img + off, d_targets + off, G.n, H, W, cfg->ssim_weight, gimg + off,
+                            loss + b, nullptr, base + G.loss_scratch, s),
+          "batch: image loss");
+    off += (int64_t)G.n * H * W;
+  }
+  return IGS_OK;
+}
+
+// The packed parameters [N][5+n] (and the gradient, if given) must match the
+// shape's Gaussian count and be 16-byte aligned.
+int check_params(const float* params, const float* grad, const BatchGeom& G, int64_t N) {
+  if (N != G.Ntot)
+    return bfail(IGS_ERR_INVALID_ARG, "batch: N = %lld differs from the shape's sum %lld",
+                 (long long)N, (long long)G.Ntot);
+  if ((uintptr_t)params % 16 || (uintptr_t)grad % 16)
+    return bfail(IGS_ERR_ALIGN, "batch: parameter arrays must be 16-byte aligned");
+  return IGS_OK;
+}
+
 }  // namespace
 
 }  // namespace igs
 
 using namespace igs;
+
+extern "C" int igs_render_forward_batch(const float* d_params, int64_t N,
+                                        const igs_batch_shape* shape, const igs_config* cfg,
+                                        void* ws, size_t ws_bytes, int64_t m_capacity,
+                                        float* d_imgs, igs_stream stream) {
+  BatchGeom G;
+  if (int r = batch_geom(shape, cfg, m_capacity, &G)) return r;
+  if (int r = check_ws(G, ws, ws_bytes)) return r;
+  if (!d_params || !d_imgs) return bfail(IGS_ERR_INVALID_ARG, "batch forward: NULL pointer");
+  if (int r = check_params(d_params, nullptr, G, N)) return r;
+  if ((uintptr_t)d_imgs % 4) return bfail(IGS_ERR_ALIGN, "batch forward: images misaligned");
+  char* base = static_cast<char*>(ws);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  RenderParams rp;
+  // lists longer than one forward stage (256) are sorted by index
+  if (int r = batch_bin(d_params, G, cfg, base, m_capacity, BATCH_TILE * BATCH_TILE, &rp, s))
+    return r;
+  return batch_forward(G, cfg, base, rp, d_imgs, s);
+}
+
+extern "C" int igs_render_backward_batch(const float* d_params, int64_t N,
+                                         const float* d_grad_imgs, const igs_batch_shape* shape,
+                                         const igs_config* cfg, const igs_batch_tuning* tuning,
+                                         void* ws, size_t ws_bytes, int64_t m_capacity,
+                                         float* d_grad, igs_stream stream) {
+  BatchGeom G;
+  if (int r = batch_geom(shape, cfg, m_capacity, &G)) return r;
+  if (int r = check_ws(G, ws, ws_bytes)) return r;
+  if (!d_params || !d_grad_imgs || !d_grad)
+    return bfail(IGS_ERR_INVALID_ARG, "batch backward: NULL pointer");
+  if (int r = check_params(d_params, d_grad, G, N)) return r;
+  if ((uintptr_t)d_grad_imgs % 4) return bfail(IGS_ERR_ALIGN, "batch backward: gradient misaligned");
+  igs_batch_tuning tn = tuning ? *tuning : igs_batch_tuning{4, 256, 0};
+  if (int r = check_tuning(tn)) return r;
+  char* base = static_cast<char*>(ws);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  RenderParams rp;
+  if (int r = batch_bin(d_params, G, cfg, base, m_capacity, tn.stage, &rp, s)) return r;
+  return batch_adjoint(d_grad, nullptr, d_grad_imgs, G, cfg, tn, base, rp, s);
+}
 
 extern "C" int igs_batch_workspace_size(const igs_batch_shape* shape, const igs_config* cfg,
                                         int64_t m_capacity, size_t* bytes) {
@@ -278,8 +385,17 @@ extern "C" int igs_fit_batch_step(const igs_fit_state* st, const float* d_target
   char* base = static_cast<char*>(ws);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   RenderParams rp;
-  if (int r = batch_bin(st, G, cfg, base, m_capacity, tn.stage, &rp, s)) return r;
-  if (int r = batch_adjoint(st, d_targets, G, cfg, tn, base, rp, s)) return r;
+  if (int r = batch_bin(st->params, G, cfg, base, m_capacity, tn.stage, &rp, s)) return r;
+  if (cfg->ssim_weight > 0.0f) {
+    if (int r = batch_forward(G, cfg, base, rp, reinterpret_cast<float*>(base + G.img), s))
+      return r;
+    if (int r = batch_image_loss(G, shape, cfg, d_targets, base, s)) return r;
+    if (int r = batch_adjoint(st->grad, nullptr, reinterpret_cast<const float*>(base + G.gimg),
+                              G, cfg, tn, base, rp, s))
+      return r;
+  } else {
+    if (int r = batch_adjoint(st->grad, d_targets, nullptr, G, cfg, tn, base, rp, s)) return r;
+  }
   if (int r = igs_adam_update(st, cfg, stream)) return r;
   BCUDA(launch_finalize_batch(st->step, reinterpret_cast<const double*>(base + G.loss),
                               reinterpret_cast<const int4*>(base + G.dims), G.B, G.n, d_loss_out,
@@ -302,7 +418,7 @@ extern "C" int igs_autotune_batch(const igs_fit_state* st, const float* d_target
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   RenderParams rp;
   // one binning serves every stage tried below
-  if (int r = batch_bin(st, G, cfg, base, m_capacity, BATCH_MIN_STAGE, &rp, s)) return r;
+  if (int r = batch_bin(st->params, G, cfg, base, m_capacity, BATCH_MIN_STAGE, &rp, s)) return r;
   cudaEvent_t e0, e1;
   BCUDA(cudaEventCreate(&e0), "autotune: event");
   BCUDA(cudaEventCreate(&e1), "autotune: event");
@@ -316,11 +432,11 @@ extern "C" int igs_autotune_batch(const igs_fit_state* st, const float* d_target
       for (int stg : stages) {
         if (rc != IGS_OK) break;
         const igs_batch_tuning tn{c, stg, order};
-        rc = batch_adjoint(st, d_targets, G, cfg, tn, base, rp, s);  // warm-up
+        rc = batch_adjoint(st->grad, d_targets, nullptr, G, cfg, tn, base, rp, s);  // warm-up
         if (rc) break;
         cudaEventRecord(e0, s);
         for (int i = 0; i < reps && rc == IGS_OK; ++i)
-          rc = batch_adjoint(st, d_targets, G, cfg, tn, base, rp, s);
+          rc = batch_adjoint(st->grad, d_targets, nullptr, G, cfg, tn, base, rp, s);
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) {
           rc = bfail(IGS_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));

@@ -107,6 +107,19 @@ __global__ void __launch_bounds__(256) k_preprocess(PrepParams p) {
   g.b = make_float4(A11, r, t1, t2);
   p.rec[i] = g;
   p.trig[i] = make_float2(c, s);
+  if constexpr (sizeof(T) == 2) {
+    if (p.rec16) {
+      HRec h;
+      h.mu = (unsigned)reinterpret_cast<const unsigned short&>(xy[0]) |
+             ((unsigned)reinterpret_cast<const unsigned short&>(xy[1]) << 16);
+      h.A00 = A00;
+      h.B = B;
+      h.A11 = A11;
+      p.rec16[i] = h;
+      for (int ch = 0; ch < p.n; ++ch)
+        p.col16[i * p.n + ch] = reinterpret_cast<const unsigned short&>(cp[ch]);
+    }
+  }
 }
 
 template <bool BATCH>

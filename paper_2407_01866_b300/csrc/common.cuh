@@ -23,6 +23,21 @@ struct __align__(16) GRec {
   float4 b;
 };
 
+// Hot record of a Gaussian stored in float16 or bfloat16: the stored bits of
+// mu (x low, y high) and the binary32 conic. mu in pixels is recomputed with
+// the same binary32 product as preprocessing, so the ranking key is the one
+// computed from a GRec, from half the bytes.
+struct __align__(16) HRec {
+  unsigned int mu;
+  float A00, B, A11;
+};
+
+// Binary32 value of a stored half-precision bit pattern (hdt 1: float16,
+// 2: bfloat16); both convert exactly.
+__device__ __forceinline__ float half_bits_to_f32(unsigned short h, int hdt) {
+  return hdt == 2 ? __uint_as_float((unsigned)h << 16) : __half2float(__ushort_as_half(h));
+}
+
 // Device status block at the head of every workspace. The first 32 bytes
 // have the layout of igs_stats in include/imgs.h.
 struct DevStatus {

@@ -16,7 +16,7 @@ constexpr int SCAN_ITEMS = SCAN_THREADS * SCAN_PER_THREAD;
 
 // Byte offsets of the workspace sections (all 256-byte aligned).
 struct WsLayout {
-  size_t status, rec, trig, color, tcnt, toff, part, vals, tmp, big, wide, range;
+  size_t status, rec, trig, color, rec16, col16, tcnt, toff, part, vals, tmp, big, wide, range;
   size_t total;
   int64_t part_len;     // scan partials entries
   int tiles_x, tiles_y;
@@ -38,6 +38,10 @@ struct PrepParams {
   GRec* rec;
   float2* trig;
   float* color_out;
+  // half-precision storage only: the hot record of the render and decode
+  // loops (stored mu bits, binary32 conic) and the stored colour bits
+  HRec* rec16;
+  unsigned short* col16;
   unsigned int* tcnt;           // [T] hits per tile (zeroed before preprocess)
   unsigned long long* toff;     // [T] start of each tile's segment
   unsigned int* vals;           // [m_cap] Gaussian index per intersection
@@ -59,6 +63,12 @@ struct RenderParams {
   const GRec* rec;
   const float2* trig;
   const float* color;  // [N][n]
+  // half-precision storage (hdt = 1: float16, 2: bfloat16; 0: none): the
+  // render and decode loops read these 16-byte records and 2-byte colours
+  // instead of rec / color (same binary32 values)
+  const HRec* rec16;
+  const unsigned short* col16;
+  int hdt;
   int H, W, tiles_x, tiles_y, n;
   int N;                   // number of Gaussians (bounds guard on list entries)
   int normalize;           // 1: Eq. 5; 0: unnormalised sum over the kept Gaussians
@@ -119,6 +129,9 @@ cudaError_t launch_render_bwd(const RenderParams& p, int tile, int K, cudaStream
 // Persistent adjoint over a batch of images (16x16 tiles); stage in {64,128,256}.
 cudaError_t launch_render_bwd_batch(const RenderParams& p, const BatchTables& bt, int K,
                                     int stage, int grid, cudaStream_t s);
+// Forward render of every tile of a batch of images (16x16 tiles).
+cudaError_t launch_render_fwd_batch(const RenderParams& p, const BatchTables& bt, int K,
+                                    cudaStream_t s);
 cudaError_t launch_decode(const RenderParams& p, int K, cudaStream_t s);
 bool render_supported(int tile, int K, int n);
 

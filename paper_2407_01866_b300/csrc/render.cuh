@@ -127,6 +127,32 @@ __device__ __forceinline__ float warp_max_key(float v) {
   return __uint_as_float(__reduce_max_sync(FULL_MASK, __float_as_uint(fmaxf(v, 0.0f))));
 }
 
+// Ranking geometry of Gaussian gid, a = (mx, my, A00, B) and A11, from the
+// records the launch reads: the 16-byte hot record of half-precision storage
+// (mu in pixels recomputed with preprocessing's binary32 product), else the
+// float32 record. Both give the same binary32 values.
+__device__ __forceinline__ void load_geom(const RenderParams& p, int gid, float4& a, float& a11) {
+  if (p.hdt) {
+    const HRec h = p.rec16[gid];
+    a = make_float4(__fmul_rn(half_bits_to_f32((unsigned short)(h.mu & 0xffffu), p.hdt),
+                              (float)p.W),
+                    __fmul_rn(half_bits_to_f32((unsigned short)(h.mu >> 16), p.hdt),
+                              (float)p.H),
+                    h.A00, h.B);
+    a11 = h.A11;
+  } else {
+    const GRec g = p.rec[gid];
+    a = g.a;
+    a11 = g.b.x;
+  }
+}
+
+// Channel c of Gaussian gid's colour (stored half-precision bits, or float32).
+__device__ __forceinline__ float load_colour(const RenderParams& p, int gid, int c, int n) {
+  return p.hdt ? half_bits_to_f32(p.col16[(int64_t)gid * n + c], p.hdt)
+               : p.color[(int64_t)gid * n + c];
+}
+
 // Colours of staged candidates live in shared memory, candidate-major
 // s_col[j * col_stride(NC) + c], when the channel count is a compile-time
 // constant; three channels are padded to a float4 (one 16-byte load).
@@ -140,13 +166,15 @@ __device__ __forceinline__ void stage_chunk(const RenderParams& p, int base, int
   if (j < cnt) {
     const int gid = p.list[base + j];
     if ((unsigned)gid < (unsigned)p.N) {
-      const GRec g = p.rec[gid];
-      s_a[j] = g.a;
-      s_b[j] = make_float2(g.b.x, __int_as_float(gid));
+      float4 a;
+      float a11;
+      load_geom(p, gid, a, a11);
+      s_a[j] = a;
+      s_b[j] = make_float2(a11, __int_as_float(gid));
       if (NC > 0) {
 #pragma unroll
         for (int c = 0; c < (NC > 0 ? NC : 1); ++c)
-          s_col[j * col_stride(NC) + c] = p.color[(int64_t)gid * NC + c];
+          s_col[j * col_stride(NC) + c] = load_colour(p, gid, c, NC);
       }
     } else {  // corrupt list entry: a NaN key is never selected
       s_a[j] = make_float4(__int_as_float(0x7fc00000), 0.f, 0.f, 0.f);
@@ -170,7 +198,8 @@ __device__ __forceinline__ void stage_sorted(const RenderParams& p, int base, in
                                              float* s_col, unsigned* s_key) {
   constexpr int NCS = NC > 0 ? NC : 1;
   const int j = threadIdx.x;
-  GRec g;
+  float4 ga;
+  float ga11 = 0.0f;
   float col[NCS];
   int gid = -1;
   unsigned key = 0xffffffffu, kid = 0xffffffffu;  // padding: after every real entry
@@ -180,12 +209,12 @@ __device__ __forceinline__ void stage_sorted(const RenderParams& p, int base, in
     if ((unsigned)e < (unsigned)p.N) {
       kid = (unsigned)e;
       gid = e;
-      g = p.rec[gid];
+      load_geom(p, gid, ga, ga11);
       if (NC > 0) {
 #pragma unroll
-        for (int c = 0; c < NCS; ++c) col[c] = p.color[(int64_t)gid * NC + c];
+        for (int c = 0; c < NCS; ++c) col[c] = load_colour(p, gid, c, NC);
       }
-      key = __float_as_uint(fmaxf(rank_key(cx, cy, g.a.x, g.a.y, g.a.z, g.a.w, g.b.x), 0.0f));
+      key = __float_as_uint(fmaxf(rank_key(cx, cy, ga.x, ga.y, ga.z, ga.w, ga11), 0.0f));
     }
   }
   // 64-bit (key, index) words: one unsigned compare orders them
@@ -201,9 +230,9 @@ __device__ __forceinline__ void stage_sorted(const RenderParams& p, int base, in
       r += (v.x < mine ? 1 : 0) + (v.y < mine ? 1 : 0);
     }
     if (gid >= 0) {
-      s_a[r] = g.a;
-      s_b[r] = make_float2(g.b.x, __int_as_float(gid));
-      s_e[r] = make_float2(0.5f / g.a.z, 0.5f / g.b.x);
+      s_a[r] = ga;
+      s_b[r] = make_float2(ga11, __int_as_float(gid));
+      s_e[r] = make_float2(0.5f / ga.z, 0.5f / ga11);
       if (NC > 0) {
 #pragma unroll
         for (int c = 0; c < NCS; ++c) s_col[r * col_stride(NC) + c] = col[c];
@@ -819,29 +848,35 @@ __device__ __forceinline__ int record_winners(const int (&tq)[K], bool live, uns
   return nw;
 }
 
+// Where one tile of one image lives (the batched form renders many images).
+struct TileCtx {
+  int2 range;        // [start, end) of the tile's list
+  int x0, y0;        // tile origin in pixels
+  int H, W;          // its image
+  int64_t off;       // offset (floats) of the image in img / target / grad_img
+  float inv_count;   // 1 / (H W n)
+  double* loss_acc;  // where the tile adds sum |c_r - c_t|
+};
+
+// Forward render of one tile (its pixels' Eq. 5 colours into p.img at the
+// tile's image offset), with the staged arrays in shared memory.
 template <int TILE, int K, int NC>
-__global__ void __launch_bounds__(TILE * TILE, TILE == 16 ? 6 : 16) k_render_fwd(RenderParams p) {
+__device__ __forceinline__ void fwd_tile(const RenderParams& p, const TileCtx& t, float4* s_a,
+                                         float2* s_b, float2* s_e, unsigned* s_key,
+                                         float* s_col) {
   constexpr int NT = TILE * TILE;
-  __shared__ float4 s_a[NT];
-  __shared__ float2 s_b[NT];
-  __shared__ float2 s_e[NT];
-  __shared__ __align__(16) unsigned s_key[2 * NT];
-  __shared__ __align__(16) float s_col[NT * col_stride(NC)];
-  const int tile_id = blockIdx.x;
-  const int x0 = (tile_id % p.tiles_x) * TILE, y0 = (tile_id / p.tiles_x) * TILE;
   const int2 lp = pixel_of<TILE>(threadIdx.x);
-  const int x = x0 + lp.x, y = y0 + lp.y;
+  const int x = t.x0 + lp.x, y = t.y0 + lp.y;
   const float px = (float)x + 0.5f, py = (float)y + 0.5f;
-  const bool in_img = x < p.W && y < p.H;
-  const int2 range = p.range[tile_id];
-  const int len = range.y - range.x;
+  const bool in_img = x < t.W && y < t.H;
+  const int len = t.range.y - t.range.x;
   float tq[KS<K>::A];
   PixelBlend<Chan<NC>::R> r;
   if (len <= NT) {
-    stage_sorted<NT, NC>(p, range.x, len, (float)x0 + 0.5f * TILE, (float)y0 + 0.5f * TILE,
-                         s_a, s_b, s_e, s_col, s_key);
+    stage_sorted<NT, NC>(p, t.range.x, len, (float)t.x0 + 0.5f * TILE,
+                         (float)t.y0 + 0.5f * TILE, s_a, s_b, s_e, s_col, s_key);
     __syncthreads();
-    const float4 R = block_rect<TILE>(x0, y0);
+    const float4 R = block_rect<TILE>(t.x0, t.y0);
     if constexpr (K > 0) {
       int tk[K];
       int md;
@@ -856,27 +891,38 @@ __global__ void __launch_bounds__(TILE * TILE, TILE == 16 ? 6 : 16) k_render_fwd
                                          s_col, nullptr, nullptr, r);
     }
   } else {
-    select_keys<TILE, K, NT>(p, range, px, py, tq, s_a, s_b);
-    blend_pass<TILE, K, NC, NT>(p, range, px, py, tq, r, s_a, s_b, s_col);
+    select_keys<TILE, K, NT>(p, t.range, px, py, tq, s_a, s_b);
+    blend_pass<TILE, K, NC, NT>(p, t.range, px, py, tq, r, s_a, s_b, s_col);
   }
   if (!in_img) return;
   const int n = nchan<NC>(p);
-  const int64_t plane = (int64_t)p.H * p.W;
-  const int64_t o = (int64_t)y * p.W + x;
+  const int64_t plane = (int64_t)t.H * t.W;
+  const int64_t o = t.off + (int64_t)y * t.W + x;
 #pragma unroll
   for (int c = 0; c < Chan<NC>::R; ++c)
     if (NC > 0 || c < n) p.img[c * plane + o] = r.cr[c];
 }
 
-// Where one tile of one image lives (the batched form renders many images).
-struct TileCtx {
-  int2 range;        // [start, end) of the tile's list
-  int x0, y0;        // tile origin in pixels
-  int H, W;          // its image
-  int64_t off;       // offset (floats) of the image in img / target / grad_img
-  float inv_count;   // 1 / (H W n)
-  double* loss_acc;  // where the tile adds sum |c_r - c_t|
-};
+template <int TILE, int K, int NC>
+__global__ void __launch_bounds__(TILE * TILE, TILE == 16 ? 6 : 16) k_render_fwd(RenderParams p) {
+  constexpr int NT = TILE * TILE;
+  __shared__ float4 s_a[NT];
+  __shared__ float2 s_b[NT];
+  __shared__ float2 s_e[NT];
+  __shared__ __align__(16) unsigned s_key[2 * NT];
+  __shared__ __align__(16) float s_col[NT * col_stride(NC)];
+  const int tile_id = blockIdx.x;
+  TileCtx t;
+  t.range = p.range[tile_id];
+  t.x0 = (tile_id % p.tiles_x) * TILE;
+  t.y0 = (tile_id / p.tiles_x) * TILE;
+  t.H = p.H;
+  t.W = p.W;
+  t.off = 0;
+  t.inv_count = p.inv_count;
+  t.loss_acc = nullptr;
+  fwd_tile<TILE, K, NC>(p, t, s_a, s_b, s_e, s_key, s_col);
+}
 
 // Dynamic shared-memory layout of the adjoint kernel (in 4-byte words), for
 // NT pixels, n channels and CH Gaussians per stage (64 <= CH <= NT).
@@ -1433,6 +1479,32 @@ __global__ void __launch_bounds__(TILE * TILE, 5) k_render_bwd_batch(RenderParam
   }
 }
 
+// Forward render of the concatenated tiles of many images, one CTA per tile.
+template <int TILE, int K, int NC>
+__global__ void __launch_bounds__(TILE * TILE, 6) k_render_fwd_batch(RenderParams p,
+                                                                    BatchTables bt) {
+  constexpr int NT = TILE * TILE;
+  __shared__ float4 s_a[NT];
+  __shared__ float2 s_b[NT];
+  __shared__ float2 s_e[NT];
+  __shared__ __align__(16) unsigned s_key[2 * NT];
+  __shared__ __align__(16) float s_col[NT * col_stride(NC)];
+  const int it = blockIdx.x;
+  const int b = image_of_tile(bt, it);
+  const int4 dm = bt.dims[b];
+  const int local = it - bt.tile_off[b];
+  TileCtx t;
+  t.range = p.range[it];
+  t.x0 = (local % dm.z) * TILE;
+  t.y0 = (local / dm.z) * TILE;
+  t.H = dm.x;
+  t.W = dm.y;
+  t.off = bt.pix_off[b];
+  t.inv_count = 0.0f;
+  t.loss_acc = nullptr;
+  fwd_tile<TILE, K, NC>(p, t, s_a, s_b, s_e, s_key, s_col);
+}
+
 // One thread per query point: its tile's list is walked from global memory.
 template <int K, int NC>
 __global__ void __launch_bounds__(256) k_decode(RenderParams p) {
@@ -1456,20 +1528,23 @@ __global__ void __launch_bounds__(256) k_decode(RenderParams p) {
       for (int j = range.x; j < range.y; ++j) {
         const int id = p.list[j];
         if ((unsigned)id >= (unsigned)p.N) continue;
-        const GRec g = p.rec[id];
-        q0 = fminf(q0, rank_key(px, py, g.a.x, g.a.y, g.a.z, g.a.w, g.b.x));
+        float4 a;
+        float a11;
+        load_geom(p, id, a, a11);
+        q0 = fminf(q0, rank_key(px, py, a.x, a.y, a.z, a.w, a11));
       }
     }
     for (int j = range.x; j < range.y; ++j) {
       const int id = p.list[j];
       if ((unsigned)id >= (unsigned)p.N) continue;
-      const GRec g = p.rec[id];
-      const float w = blend_weight(q0, rank_key(px, py, g.a.x, g.a.y, g.a.z, g.a.w, g.b.x));
+      float4 a;
+      float a11;
+      load_geom(p, id, a, a11);
+      const float w = blend_weight(q0, rank_key(px, py, a.x, a.y, a.z, a.w, a11));
       Z += w;
-      const float* col = p.color + (int64_t)id * n;
 #pragma unroll
       for (int c = 0; c < NCR; ++c)
-        if (NC > 0 || c < n) cr[c] = fmaf(w, col[c], cr[c]);
+        if (NC > 0 || c < n) cr[c] = fmaf(w, load_colour(p, id, c, n), cr[c]);
     }
   } else {
     float tq[KS<K>::A];
@@ -1479,23 +1554,25 @@ __global__ void __launch_bounds__(256) k_decode(RenderParams p) {
       tq[k] = F_INF;
       tp[k] = -1;
     }
-    // four candidates per round: their index and record loads are in flight
+    // DU candidates per round: their index and record loads are in flight
     // together (the walk is bound by dependent L2 latencies)
-    for (int j0 = range.x; j0 < range.y; j0 += 4) {
-      int id[4];
-      float q[4];
+    constexpr int DU = 4;
+    for (int j0 = range.x; j0 < range.y; j0 += DU) {
+      int id[DU];
+      float q[DU];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) id[u] = j0 + u < range.y ? p.list[j0 + u] : -1;
+      for (int u = 0; u < DU; ++u) id[u] = j0 + u < range.y ? p.list[j0 + u] : -1;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < DU; ++u) {
         const bool ok = (unsigned)id[u] < (unsigned)p.N;
-        const float4 a = ok ? p.rec[id[u]].a : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float a11 = ok ? p.rec[id[u]].b.x : 0.0f;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        float a11 = 0.0f;
+        if (ok) load_geom(p, id[u], a, a11);
         q[u] = ok ? rank_key(px, py, a.x, a.y, a.z, a.w, a11) : F_INF;
         if (!ok) id[u] = -1;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < DU; ++u) {
         if (id[u] < 0) continue;
         if (q[u] < tq[KS<K>::A - 1] || (q[u] == tq[KS<K>::A - 1] && id[u] < tp[KS<K>::A - 1]))
           topk_insert<KS<K>::A>(tq, tp, q[u], id[u]);
@@ -1507,10 +1584,9 @@ __global__ void __launch_bounds__(256) k_decode(RenderParams p) {
       if (tp[k] >= 0) {
         const float w = blend_weight(q0, tq[k]);
         Z += w;
-        const float* col = p.color + (int64_t)tp[k] * n;
 #pragma unroll
         for (int c = 0; c < NCR; ++c)
-          if (NC > 0 || c < n) cr[c] = fmaf(w, col[c], cr[c]);
+          if (NC > 0 || c < n) cr[c] = fmaf(w, load_colour(p, tp[k], c, n), cr[c]);
       }
     }
   }

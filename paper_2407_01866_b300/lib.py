@@ -58,7 +58,9 @@ class Bins(ctypes.Structure):
                 ("N", ctypes.c_int64), ("m_capacity", ctypes.c_int64),
                 ("tile_range", ctypes.c_void_p), ("list", ctypes.c_void_p),
                 ("rec", ctypes.c_void_p), ("trig", ctypes.c_void_p),
-                ("color", ctypes.c_void_p), ("status", ctypes.c_void_p)]
+                ("color", ctypes.c_void_p), ("status", ctypes.c_void_p),
+                ("dtype", ctypes.c_int32), ("rec16", ctypes.c_void_p),
+                ("color16", ctypes.c_void_p)]
 
 
 class FitState(ctypes.Structure):
@@ -120,6 +122,12 @@ _SIGNATURES = {
     "igs_static_scratch_bytes": ([ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "igs_batch_workspace_size": ([ctypes.POINTER(BatchShape), ctypes.POINTER(Config),
                                   ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "igs_render_forward_batch": ([_P, ctypes.c_int64, ctypes.POINTER(BatchShape),
+                                  ctypes.POINTER(Config), _P, ctypes.c_size_t, ctypes.c_int64,
+                                  _P, _P], ctypes.c_int),
+    "igs_render_backward_batch": ([_P, ctypes.c_int64, _P, ctypes.POINTER(BatchShape),
+                                   ctypes.POINTER(Config), ctypes.POINTER(BatchTuning), _P,
+                                   ctypes.c_size_t, ctypes.c_int64, _P, _P], ctypes.c_int),
     "igs_batch_setup": ([ctypes.POINTER(BatchShape), ctypes.POINTER(Config), _P, ctypes.c_size_t,
                          ctypes.c_int64, _P], ctypes.c_int),
     "igs_fit_batch_step": ([ctypes.POINTER(FitState), _P, ctypes.POINTER(BatchShape),
@@ -342,6 +350,25 @@ def fit_batch_step(state, targets, shape, cfg, ws, m_capacity, tuning=None, loss
     _check(load().igs_fit_batch_step(ctypes.byref(state), _ptr(targets), ctypes.byref(shape),
                                      ctypes.byref(cfg), tp, _ptr(ws), ws.numel(), m_capacity,
                                      _ptr(loss_out), _stream(stream)))
+
+
+def render_forward_batch(params, shape, cfg, ws, m_capacity, imgs, stream=None):
+    """Renders every image of the batch (packed params [N, 5+n]) into imgs,
+    the concatenated planar images."""
+    _check(load().igs_render_forward_batch(_ptr(params), params.shape[0], ctypes.byref(shape),
+                                           ctypes.byref(cfg), _ptr(ws), ws.numel(), m_capacity,
+                                           _ptr(imgs), _stream(stream)))
+
+
+def render_backward_batch(params, grad_imgs, shape, cfg, ws, m_capacity, grad, tuning=None,
+                          stream=None):
+    """Adjoint of every image of the batch for the upstream gradient
+    grad_imgs (laid out like the rendered images); grad [N, 5+n] receives dL/dp."""
+    tp = ctypes.byref(tuning) if tuning is not None else None
+    _check(load().igs_render_backward_batch(_ptr(params), params.shape[0], _ptr(grad_imgs),
+                                            ctypes.byref(shape), ctypes.byref(cfg), tp,
+                                            _ptr(ws), ws.numel(), m_capacity, _ptr(grad),
+                                            _stream(stream)))
 
 
 def autotune_batch(state, targets, shape, cfg, ws, m_capacity, reps=3, stream=None):

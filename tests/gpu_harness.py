@@ -73,3 +73,18 @@ def grad_rel_error(got, ref):
         s = np.abs(r).max() if r.size else 0.0
         out[name] = d / s if s > 0 else d
     return out
+
+
+def grad_elem_rel_error(got, ref, floor=1e-6):
+    """Per-element relative error per parameter group: the largest
+    |got - ref| / max(|ref|, floor * max|ref| over the group)."""
+    out = {}
+    for name, sl in GROUPS:
+        r = ref[:, sl]
+        if not r.size:
+            out[name] = 0.0
+            continue
+        s = np.abs(r).max()
+        den = np.maximum(np.abs(r), floor * s) if s > 0 else np.ones_like(r)
+        out[name] = float((np.abs(got[:, sl] - r) / den).max())
+    return out

@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-from gpu_harness import grad_rel_error  # noqa: E402
+from gpu_harness import grad_elem_rel_error, grad_rel_error  # noqa: E402
 
 PIX_TOL = 1e-5
 HALF_TOL = 2e-3
@@ -76,7 +76,10 @@ def test_fullsize_forward_and_adjoint_on_sampled_pixels(name):
     grad = torch.empty((r["N"], 5 + r["n"]), device="cuda")
     L.render_backward(r["view"], r["bins"], r["cfg"], gimg, None, grad)
     ref = O.backward_pixels(r["g"], r["pix"], vals.astype(np.float64), r["H"], r["W"])
-    errs = grad_rel_error(grad.cpu().numpy().astype(np.float64), ref)
+    got = grad.cpu().numpy().astype(np.float64)
+    errs = grad_rel_error(got, ref)
+    elem = grad_elem_rel_error(got, ref)
+    print(f"{name}: normwise {errs}, per element (floor 1e-6 max|g|) {elem}")
     assert max(errs.values()) <= GRAD_TOL, errs
 
 
@@ -99,11 +102,40 @@ def test_fullsize_fused_l1_equals_adjoint_of_its_own_sign_gradient():
     assert abs(st.loss_sum * inv - loss) <= 1e-6 * max(1.0, loss)
 
 
+def test_fullsize_fused_l1_adjoint_matches_oracle_on_sampled_pixels():
+    """The fused L1 loss and adjoint at 2048^2 against the oracle. The target
+    equals the forward rendering everywhere except at sampled pixels, so the
+    L1 gradient sign(c_r - c_t)/(HWn) is zero elsewhere (sign(0) = 0); at the
+    sampled pixels the target is the oracle's colour moved by 1e-3, whose sign
+    the oracle fixes. The oracle's gradient over those pixels is then exact."""
+    r = run_config("fit2048_rgb", seed=2, n_pix=1024, n_tiles=1)
+    H, W, n = r["H"], r["W"], r["n"]
+    want = O.render_pixels(r["g"], r["pix"], H, W)
+    assert np.abs(r["got"] - want).max() <= PIX_TOL
+    delta = np.where(np.random.default_rng(8).random(want.shape) < 0.5, -1e-3, 1e-3)
+    target = r["img"].clone()
+    pt = torch.from_numpy(r["pix"]).cuda()
+    target[:, pt[:, 0], pt[:, 1]] = torch.from_numpy((want + delta).T.astype(np.float32)).cuda()
+    grad = torch.empty((r["N"], 5 + n), device="cuda")
+    L.render_backward(r["view"], r["bins"], r["cfg"], None, target, grad)
+    st = L.read_stats(r["bins"])
+    inv = 1.0 / (H * W * n)
+    ref = O.backward_pixels(r["g"], r["pix"], -np.sign(delta) * inv, H, W)
+    got = grad.cpu().numpy().astype(np.float64)
+    errs = grad_rel_error(got, ref)
+    print(f"fused L1 at 2048^2: normwise {errs}, per element {grad_elem_rel_error(got, ref)}")
+    assert max(errs.values()) <= GRAD_TOL, errs
+    # loss: the sampled pixels' |d| (1e-3 each, within the pixel tolerance)
+    want_loss = np.abs(delta).sum() * inv
+    assert abs(st.loss_sum * inv - want_loss) <= PIX_TOL * delta.size * inv
+
+
 @pytest.mark.parametrize("dt", [torch.float16, torch.bfloat16])
 def test_decode8192_half_storage_pixels_and_points(dt):
     r = run_config("decode8192_rgb", seed=0, dtype=dt, n_pix=512, n_tiles=2)
     want = O.render_pixels(r["g"], r["pix"], r["H"], r["W"])
     err = np.abs(r["got"] - want).max()
+    print(f"8192^2 {dt}: max |pixel - oracle| {err:.2e}")
     assert err <= HALF_TOL and err <= PIX_TOL, err
     pts = synth.query_points(1_000_000, r["H"], r["W"], seed=0)
     q = torch.from_numpy(pts).cuda()
@@ -111,4 +143,6 @@ def test_decode8192_half_storage_pixels_and_points(dt):
     L.decode_points(r["bins"], r["cfg"], q, out)
     sel = np.random.default_rng(5).choice(len(pts), 512, replace=False)
     want = O.render_points(r["g"], pts[sel].astype(np.float64), r["H"], r["W"])
-    assert np.abs(out.cpu().numpy()[sel] - want).max() <= PIX_TOL
+    qerr = np.abs(out.cpu().numpy()[sel] - want).max()
+    print(f"8192^2 {dt}: max |decoded point - oracle| {qerr:.2e}")
+    assert qerr <= PIX_TOL
