@@ -28,6 +28,8 @@ WORKLOAD = dict(name="fit2048_rgb", H=2048, W=2048, n=3, N=100_000, n_sin=8, n_r
                 noise=3, seed=0)
 FIT_WORKLOADS = {
     "fit2048_rgb": WORKLOAD,
+    "fit256_rgb": dict(name="fit256_rgb", H=256, W=256, n=3, N=4096, n_sin=8, n_rect=20,
+                       noise=0, seed=0),
     "fit4096_tex9": dict(name="fit4096_tex9", H=4096, W=4096, n=9, N=500_000, n_sin=8,
                          n_rect=200, noise=3, seed=0),
 }

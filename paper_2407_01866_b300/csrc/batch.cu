@@ -35,9 +35,10 @@ struct BatchGeom {
   WsLayout L;
   size_t dims, tile_off, pix_off, gauss_off, img_of, loss, work, total;
   // SSIM fits only (0 otherwise): renderings, their loss gradients, and the
-  // image-loss scratch of the largest image
-  size_t img, gimg, loss_scratch;
-  int64_t Ntot, T, pixels;
+  // image loss's 32 x 32 tile tables (per image (H, W, tiles across, 0) and
+  // first tile)
+  size_t img, gimg, ssim_dims, ssim_toff;
+  int64_t Ntot, T, pixels, ssim_tiles;
   int B, n, Hmax, Wmax;
 };
 
@@ -91,12 +92,15 @@ int batch_geom(const igs_batch_shape* sh, const igs_config* cfg, int64_t m_cap, 
   G->img_of = o;    o = up256(o + sizeof(int) * (size_t)N);
   G->loss = o;      o = up256(o + sizeof(double) * B);
   G->work = o;      o = up256(o + sizeof(unsigned int));
-  G->img = G->gimg = G->loss_scratch = 0;
+  G->img = G->gimg = G->ssim_dims = G->ssim_toff = 0;
+  G->ssim_tiles = 0;
   if (cfg->ssim_weight > 0.0f) {
     const size_t img_bytes = sizeof(float) * (size_t)sh->n * (size_t)pixels;
-    G->img = o;          o = up256(o + img_bytes);
-    G->gimg = o;         o = up256(o + img_bytes);
-    G->loss_scratch = o; o = up256(o + image_loss_scratch_bytes(sh->n, Hmax, Wmax));
+    G->img = o;       o = up256(o + img_bytes);
+    G->gimg = o;      o = up256(o + img_bytes);
+    G->ssim_dims = o; o = up256(o + sizeof(int4) * B);
+    G->ssim_toff = o; o = up256(o + sizeof(int) * (B + 1));
+    for (int b = 0; b < B; ++b) G->ssim_tiles += ssim_tiles_of(sh->H[b], sh->W[b]);
   }
   G->total = o;
   G->Ntot = N;
@@ -248,22 +252,19 @@ int batch_forward(const BatchGeom& G, const igs_config* cfg, char* base, RenderP
   return IGS_OK;
 }
 
-// L1 + w (1 - SSIM) of every rendering against its target: the image-space
-// gradients into gimg, the per-image loss sums into the batch's loss table.
-int batch_image_loss(const BatchGeom& G, const igs_batch_shape* sh, const igs_config* cfg,
-                     const float* d_targets, char* base, cudaStream_t s) {
-  BCUDA(cudaMemsetAsync(base + G.loss, 0, sizeof(double) * G.B, s), "batch: zero losses");
-  const float* img = reinterpret_cast<const float*>(base + G.img);
-  float* gimg = reinterpret_cast<float*>(base + G.gimg);
-  double* loss = reinterpret_cast<double*>(base + G.loss);
-  int64_t off = 0;
-  for (int b = 0; b < G.B; ++b) {
-    const int H = sh->H[b], W = sh->W[b];
-    BCUDA(launch_image_loss(img + off, d_targets + off, G.n, H, W, cfg->ssim_weight, gimg + off,
-                            loss + b, nullptr, base + G.loss_scratch, s),
-          "batch: image loss");
-    off += (int64_t)G.n * H * W;
-  }
+// L1 + w (1 - SSIM) of every rendering against its target, one launch over
+// the 32 x 32 loss tiles of all images: the image-space gradients into gimg,
+// the per-image loss sums into the batch's loss table.
+int batch_image_loss(const BatchGeom& G, const igs_config* cfg, const float* d_targets,
+                     char* base, cudaStream_t s) {
+  BCUDA(launch_image_loss_batch(reinterpret_cast<const float*>(base + G.img), d_targets, G.B,
+                                reinterpret_cast<const int4*>(base + G.ssim_dims),
+                                reinterpret_cast<const int*>(base + G.ssim_toff),
+                                reinterpret_cast<const long long*>(base + G.pix_off),
+                                (int)G.ssim_tiles, G.n, cfg->ssim_weight,
+                                reinterpret_cast<float*>(base + G.gimg),
+                                reinterpret_cast<double*>(base + G.loss), s),
+        "batch: image loss");
   return IGS_OK;
 }
 
@@ -365,6 +366,22 @@ extern "C" int igs_batch_setup(const igs_batch_shape* shape, const igs_config* c
   BCUDA(cudaMemcpyAsync(base + G.gauss_off, gauss_off.data(), sizeof(long long) * (B + 1),
                         cudaMemcpyHostToDevice, s),
         "batch setup: Gaussian offsets");
+  if (G.ssim_dims) {
+    std::vector<int4> sdims(B);
+    std::vector<int> stoff(B + 1);
+    stoff[0] = 0;
+    for (int b = 0; b < B; ++b) {
+      const int H = shape->H[b], W = shape->W[b];
+      sdims[b] = make_int4(H, W, 0, 0);
+      stoff[b + 1] = stoff[b] + ssim_tiles_of(H, W);
+    }
+    BCUDA(cudaMemcpyAsync(base + G.ssim_dims, sdims.data(), sizeof(int4) * B,
+                          cudaMemcpyHostToDevice, s),
+          "batch setup: loss tile sizes");
+    BCUDA(cudaMemcpyAsync(base + G.ssim_toff, stoff.data(), sizeof(int) * (B + 1),
+                          cudaMemcpyHostToDevice, s),
+          "batch setup: loss tile offsets");
+  }
   BCUDA(launch_fill_image_of(reinterpret_cast<int*>(base + G.img_of),
                              reinterpret_cast<const long long*>(base + G.gauss_off), B, G.Ntot, s),
         "batch setup: image of each Gaussian");
@@ -389,7 +406,7 @@ extern "C" int igs_fit_batch_step(const igs_fit_state* st, const float* d_target
   if (cfg->ssim_weight > 0.0f) {
     if (int r = batch_forward(G, cfg, base, rp, reinterpret_cast<float*>(base + G.img), s))
       return r;
-    if (int r = batch_image_loss(G, shape, cfg, d_targets, base, s)) return r;
+    if (int r = batch_image_loss(G, cfg, d_targets, base, s)) return r;
     if (int r = batch_adjoint(st->grad, nullptr, reinterpret_cast<const float*>(base + G.gimg),
                               G, cfg, tn, base, rp, s))
       return r;

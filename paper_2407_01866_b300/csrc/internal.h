@@ -167,6 +167,16 @@ cudaError_t launch_place(const float* target, const float* render, int H, int W,
 // sum over channels and pixels of |x - y| + w (1 - S), loss_out (nullable)
 // the mean. scratch: image_loss_scratch_bytes(n, H, W) bytes, 256-aligned.
 size_t image_loss_scratch_bytes(int n, int H, int W);
+// Number of 32 x 32 loss tiles of an H x W image.
+int ssim_tiles_of(int H, int W);
+// L1 + w (1 - SSIM) of every image of a batch in one launch (w > 0): dims
+// [B] = (H, W, 32-tiles across, 0), tile_off [B+1] the first 32-tile of each
+// image, pix_off [B+1] the images' plane offsets (floats) in x, y and grad;
+// acc [B] (zeroed here) receives each image's loss sum.
+cudaError_t launch_image_loss_batch(const float* x, const float* y, int B, const int4* dims,
+                                    const int* tile_off, const long long* pix_off, int tiles,
+                                    int n, float w_ssim, float* grad, double* acc,
+                                    cudaStream_t s);
 cudaError_t launch_image_loss(const float* x, const float* y, int n, int H, int W,
                               float w_ssim, float* grad, double* acc, float* loss_out,
                               char* scratch, cudaStream_t s);

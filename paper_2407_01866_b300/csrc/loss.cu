@@ -4,16 +4,14 @@
 //
 // SSIM is computed per channel with an 11 x 11 Gaussian window (sigma 1.5,
 // normalised, zero-padded "same" correlation) and C1 = 0.01^2, C2 = 0.03^2;
-// L_SSIM = 1 - mean SSIM over channels and pixels. Four passes, float32;
-// the horizontal ones stage row segments in shared memory, the vertical ones
-// take one thread per (channel, column, strip of RS rows):
-//   h5  horizontal window sums of x, y, x^2, y^2, x y
-//   v5  vertical sums -> mu_x, mu_y, E[x^2], E[y^2], E[xy] -> SSIM and its
-//       partials G1 = dS/dmu_x, G2 = dS/dE[x^2], G3 = dS/dE[xy]; the loss sum
-//       |x - y| + w (1 - S) is reduced into a double
-//   h3  horizontal window sums of G1..G3
-//   v3  vertical sums, then dL/dx = sign(x - y)/M - (w/M)(bG1 + 2x bG2 + y bG3)
-// (the window is symmetric: the transposed correlation is the same one).
+// L_SSIM = 1 - mean SSIM over channels and pixels. The gradient is
+//   dL/dx = sign(x - y)/M - (w/M)(bG1 + 2x bG2 + y bG3),
+// where G1 = dS/dmu_x, G2 = dS/dE[x^2], G3 = dS/dE[xy] are the SSIM partials
+// with respect to the raw window moments at each pixel (zero outside the
+// image) and bG their window sums (the window is symmetric: the transposed
+// correlation is the same one). One kernel does it per 32 x 32 tile of
+// output pixels with a halo, float32, for one image or every image of a
+// batch in one launch.
 #include <cmath>
 
 #include "internal.h"
@@ -29,178 +27,217 @@ struct Win {
   float g[2 * WR + 1];
 };
 
-// Horizontal passes: a CTA takes a row segment of HSEG outputs, stages it
-// with its halo in shared memory once, and every thread sums its taps there.
-constexpr int HSEG = 256;
+// One pass per 32 x 32 output tile: the tile's x and y with a 10-pixel halo
+// are staged in shared memory; the window moments and SSIM partials are
+// formed over the tile plus a 5-pixel ring, window-summed again over the
+// tile, and turned into the gradient. Each thread takes 3 or 4 consecutive
+// outputs of a row or column, so that staged values are reused across taps.
+constexpr int TO = 32;           // output tile edge
+constexpr int TM = TO + 2 * WR;  // 42: window moments and SSIM partials
+constexpr int TI = TO + 4 * WR;  // 52: staged x and y
+constexpr int SSIM_THREADS = 256;
+// shared memory (floats): [x | y] staged (2 TI^2), later the partials G
+// (3 TM^2); the horizontal sums of the 5 moments (5 TI TM), later those of
+// the 3 partials (3 TM TO)
+constexpr int SSIM_SA = 2 * TI * TI;
+constexpr int SSIM_SB = 5 * TI * TM;
+constexpr size_t SSIM_SMEM = sizeof(float) * (SSIM_SA + SSIM_SB);
+static_assert(3 * TM * TM <= SSIM_SA && 3 * TM * TO <= SSIM_SB, "ssim smem reuse");
 
-__global__ void __launch_bounds__(HSEG) k_h5(const float* x, const float* y, int64_t rows,
-                                             int W, Win w, int64_t total, float* out) {
-  __shared__ float sx[HSEG + 2 * WR], sy[HSEG + 2 * WR];
-  const int segs = (W + HSEG - 1) / HSEG;
-  for (int64_t b = blockIdx.x; b < rows * segs; b += gridDim.x) {
-    const int64_t row = (b / segs) * W;  // start of the (channel, row) in the planes
-    const int x0 = (int)(b % segs) * HSEG;
-    __syncthreads();
-    for (int k = threadIdx.x; k < HSEG + 2 * WR; k += blockDim.x) {
-      const int xs = x0 - WR + k;
-      const bool in = xs >= 0 && xs < W;
-      sx[k] = in ? x[row + xs] : 0.0f;
-      sy[k] = in ? y[row + xs] : 0.0f;
+// The images a launch covers: one (dims == nullptr: H, W) or a batch's
+// per-image (H, W, 32-tiles across) with first 32-tile and plane offsets.
+struct SsimImages {
+  int B;
+  const int4* dims;
+  const int* tile_off;
+  const long long* pix_off;
+  int H, W;
+};
+
+__global__ void __launch_bounds__(SSIM_THREADS) k_ssim_tile(const float* x, const float* y,
+                                                            SsimImages im, int n, Win w,
+                                                            float w_ssim, float* grad,
+                                                            double* acc) {
+  extern __shared__ __align__(16) float smem[];
+  float* sA = smem;
+  float* sB = smem + SSIM_SA;
+  const int tid = threadIdx.x;
+  // this tile's image and origin
+  int b = 0, H = im.H, W = im.W, t = blockIdx.x;
+  long long off = 0;
+  if (im.dims) {
+    int lo = 0, hi = im.B - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (im.tile_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
     }
-    __syncthreads();
-    const int xx = x0 + threadIdx.x;
-    if (xx >= W) continue;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, s4 = 0.f;
-#pragma unroll
-    for (int i = 0; i <= 2 * WR; ++i) {
-      const float a = sx[threadIdx.x + i], c = sy[threadIdx.x + i], g = w.g[i];
-      s0 = fmaf(g, a, s0);
-      s1 = fmaf(g, c, s1);
-      s2 = fmaf(g, a * a, s2);
-      s3 = fmaf(g, c * c, s3);
-      s4 = fmaf(g, a * c, s4);
-    }
-    const int64_t p = row + xx;
-    out[p] = s0;
-    out[total + p] = s1;
-    out[2 * total + p] = s2;
-    out[3 * total + p] = s3;
-    out[4 * total + p] = s4;
+    b = lo;
+    const int4 d = im.dims[b];
+    H = d.x;
+    W = d.y;
+    t = (int)blockIdx.x - im.tile_off[b];
+    off = im.pix_off[b];
   }
-}
-
-// Vertical passes: a thread covers RS consecutive rows of one column and
-// slides down them, so every loaded row feeds up to 2 WR + 1 outputs.
-constexpr int RS = 8;
-
-__global__ void __launch_bounds__(256) k_v5(const float* hm, const float* x, const float* y,
-                                            int64_t total, int n, int H, int W, Win w,
-                                            float w_ssim, float* G, double* acc) {
+  const int tx = (W + TO - 1) / TO;
+  const int x0 = (t % tx) * TO, y0 = (t / tx) * TO;
   const int64_t HW = (int64_t)H * W;
-  const int strips = (H + RS - 1) / RS;
-  const int64_t items = (int64_t)n * strips * W;
+  const float inv_m = 1.0f / ((float)n * (float)H * (float)W);
   double part = 0.0;
-  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < items;
-       it += (int64_t)gridDim.x * blockDim.x) {
-    const int xx = (int)(it % W);
-    const int64_t cs = it / W;
-    const int y0 = (int)(cs % strips) * RS;
-    const int64_t cbase = (cs / strips) * HW;
-    float m[5][RS];
+  for (int c = 0; c < n; ++c) {
+    const float* xc = x + off + c * HW;
+    const float* yc = y + off + c * HW;
+    __syncthreads();  // the previous channel is done with the staged arrays
+    for (int k = tid; k < TI * TI; k += SSIM_THREADS) {
+      const int r = y0 - 2 * WR + k / TI, q = x0 - 2 * WR + k % TI;
+      const bool in = r >= 0 && r < H && q >= 0 && q < W;
+      sA[k] = in ? xc[(int64_t)r * W + q] : 0.0f;
+      sA[TI * TI + k] = in ? yc[(int64_t)r * W + q] : 0.0f;
+    }
+    __syncthreads();
+    // horizontal window sums of x, y, x^2, y^2, x y: rows TI, columns TM
+    for (int task = tid; task < TI * (TM / 3); task += SSIM_THREADS) {
+      const int r = task / (TM / 3), j0 = (task % (TM / 3)) * 3;
+      float s[5][3];
 #pragma unroll
-    for (int k = 0; k < 5; ++k)
+      for (int m = 0; m < 5; ++m)
 #pragma unroll
-      for (int j = 0; j < RS; ++j) m[k][j] = 0.0f;
+        for (int o = 0; o < 3; ++o) s[m][o] = 0.0f;
 #pragma unroll
-    for (int rr = 0; rr < RS + 2 * WR; ++rr) {
-      const int r = y0 - WR + rr;
-      if (r < 0 || r >= H) continue;
-      const int64_t o = cbase + (int64_t)r * W + xx;
-      float v[5];
+      for (int e = 0; e < 2 * WR + 3; ++e) {
+        const float a = sA[r * TI + j0 + e], d = sA[TI * TI + r * TI + j0 + e];
+        const float aa = a * a, dd = d * d, ad = a * d;
 #pragma unroll
-      for (int k = 0; k < 5; ++k) v[k] = hm[k * total + o];
+        for (int o = 0; o < 3; ++o) {
+          const int i = e - o;  // tap of input e for output j0 + o
+          if (i < 0 || i > 2 * WR) continue;
+          const float g = w.g[i];
+          s[0][o] = fmaf(g, a, s[0][o]);
+          s[1][o] = fmaf(g, d, s[1][o]);
+          s[2][o] = fmaf(g, aa, s[2][o]);
+          s[3][o] = fmaf(g, dd, s[3][o]);
+          s[4][o] = fmaf(g, ad, s[4][o]);
+        }
+      }
 #pragma unroll
-      for (int j = 0; j < RS; ++j) {
-        const int i = rr - WR - j;  // tap offset of row r for output row y0 + j
-        if (i < -WR || i > WR) continue;
+      for (int m = 0; m < 5; ++m)
 #pragma unroll
-        for (int k = 0; k < 5; ++k) m[k][j] = fmaf(w.g[i + WR], v[k], m[k][j]);
+        for (int o = 0; o < 3; ++o) sB[(m * TI + r) * TM + j0 + o] = s[m][o];
+    }
+    __syncthreads();
+    // vertical sums -> moments -> SSIM and its partials over the TM x TM
+    // ring region (zero outside the image); the loss's SSIM term over the
+    // tile's own pixels
+    for (int task = tid; task < TM * (TM / 3); task += SSIM_THREADS) {
+      const int jm = task % TM, i0 = (task / TM) * 3;
+      float m[5][3];
+#pragma unroll
+      for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int o = 0; o < 3; ++o) m[k][o] = 0.0f;
+#pragma unroll
+      for (int e = 0; e < 2 * WR + 3; ++e) {
+        float v[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) v[k] = sB[(k * TI + i0 + e) * TM + jm];
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+          const int i = e - o;
+          if (i < 0 || i > 2 * WR) continue;
+#pragma unroll
+          for (int k = 0; k < 5; ++k) m[k][o] = fmaf(w.g[i], v[k], m[k][o]);
+        }
+      }
+#pragma unroll
+      for (int o = 0; o < 3; ++o) {
+        const int ii = i0 + o;
+        const int py = y0 - WR + ii, px = x0 - WR + jm;
+        float g1 = 0.0f, g2 = 0.0f, g3 = 0.0f;
+        if (py >= 0 && py < H && px >= 0 && px < W) {
+          const float mx = m[0][o], my = m[1][o];
+          const float vx = m[2][o] - mx * mx, vy = m[3][o] - my * my, cxy = m[4][o] - mx * my;
+          const float A1 = 2.f * mx * my + C1, A2 = 2.f * cxy + C2;
+          const float B1 = mx * mx + my * my + C1, B2 = vx + vy + C2;
+          const float iB = 1.f / (B1 * B2);
+          const float S = A1 * A2 * iB;
+          const float dS_dvx = -S / B2;
+          const float dS_dcxy = 2.f * A1 * iB;
+          const float dmx = 2.f * my * A2 * iB - S * 2.f * mx / B1;
+          g1 = dmx - 2.f * mx * dS_dvx - my * dS_dcxy;
+          g2 = dS_dvx;
+          g3 = dS_dcxy;
+          if (ii >= WR && ii < WR + TO && jm >= WR && jm < WR + TO)
+            part += (double)w_ssim * (1.0 - (double)S);
+        }
+        sA[(0 * TM + ii) * TM + jm] = g1;
+        sA[(1 * TM + ii) * TM + jm] = g2;
+        sA[(2 * TM + ii) * TM + jm] = g3;
       }
     }
+    __syncthreads();
+    // horizontal window sums of the partials: rows TM, columns TO
+    for (int task = tid; task < TM * (TO / 4); task += SSIM_THREADS) {
+      const int r = task / (TO / 4), j0 = (task % (TO / 4)) * 4;
+      float s[3][4];
 #pragma unroll
-    for (int j = 0; j < RS; ++j) {
-      if (y0 + j >= H) break;
-      const int64_t p = cbase + (int64_t)(y0 + j) * W + xx;
-      const float mx = m[0][j], my = m[1][j];
-      const float vx = m[2][j] - mx * mx, vy = m[3][j] - my * my, cxy = m[4][j] - mx * my;
-      const float A1 = 2.f * mx * my + C1, A2 = 2.f * cxy + C2;
-      const float B1 = mx * mx + my * my + C1, B2 = vx + vy + C2;
-      const float iB = 1.f / (B1 * B2);
-      const float S = A1 * A2 * iB;
-      const float dS_dvx = -S / B2;
-      const float dS_dcxy = 2.f * A1 * iB;
-      const float dmx = 2.f * my * A2 * iB - S * 2.f * mx / B1;
-      G[p] = dmx - 2.f * mx * dS_dvx - my * dS_dcxy;
-      G[total + p] = dS_dvx;
-      G[2 * total + p] = dS_dcxy;
-      part += (double)fabsf(x[p] - y[p]) + (double)w_ssim * (1.0 - (double)S);
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int o = 0; o < 4; ++o) s[k][o] = 0.0f;
+#pragma unroll
+      for (int e = 0; e < 2 * WR + 4; ++e) {
+        float v[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[k] = sA[(k * TM + r) * TM + j0 + e];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          const int i = e - o;
+          if (i < 0 || i > 2 * WR) continue;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) s[k][o] = fmaf(w.g[i], v[k], s[k][o]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int o = 0; o < 4; ++o) sB[(k * TM + r) * TO + j0 + o] = s[k][o];
+    }
+    __syncthreads();
+    // vertical sums -> dL/dx over the tile: sign(x - y)/M - (w/M)(bG1 + 2x bG2 + y bG3)
+    {
+      const int jo = tid % TO, i0 = (tid / TO) * 4;  // 256 threads: 32 columns x 8 row blocks
+      float s[3][4];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int o = 0; o < 4; ++o) s[k][o] = 0.0f;
+#pragma unroll
+      for (int e = 0; e < 2 * WR + 4; ++e) {
+        float v[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[k] = sB[(k * TM + i0 + e) * TO + jo];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          const int i = e - o;
+          if (i < 0 || i > 2 * WR) continue;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) s[k][o] = fmaf(w.g[i], v[k], s[k][o]);
+        }
+      }
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const int py = y0 + i0 + o, px = x0 + jo;
+        if (py >= H || px >= W) continue;
+        const int64_t p = (int64_t)py * W + px;
+        const float xv = xc[p], yv = yc[p];
+        const float d = xv - yv;
+        const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+        grad[off + c * HW + p] =
+            sgn * inv_m - w_ssim * inv_m * (s[0][o] + 2.f * xv * s[1][o] + yv * s[2][o]);
+        part += (double)fabsf(d);
+      }
     }
   }
   part = warp_sum<double>(part);
-  if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(acc, part);
-}
-
-__global__ void __launch_bounds__(HSEG) k_h3(const float* G, int64_t rows, int W, Win w,
-                                             int64_t total, float* out) {
-  __shared__ float sg[3][HSEG + 2 * WR];
-  const int segs = (W + HSEG - 1) / HSEG;
-  for (int64_t b = blockIdx.x; b < rows * segs; b += gridDim.x) {
-    const int64_t row = (b / segs) * W;
-    const int x0 = (int)(b % segs) * HSEG;
-    __syncthreads();
-    for (int k = threadIdx.x; k < HSEG + 2 * WR; k += blockDim.x) {
-      const int xs = x0 - WR + k;
-      const bool in = xs >= 0 && xs < W;
-#pragma unroll
-      for (int m = 0; m < 3; ++m) sg[m][k] = in ? G[m * total + row + xs] : 0.0f;
-    }
-    __syncthreads();
-    const int xx = x0 + threadIdx.x;
-    if (xx >= W) continue;
-    float acc[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int i = 0; i <= 2 * WR; ++i) {
-#pragma unroll
-      for (int m = 0; m < 3; ++m) acc[m] = fmaf(w.g[i], sg[m][threadIdx.x + i], acc[m]);
-    }
-#pragma unroll
-    for (int m = 0; m < 3; ++m) out[m * total + row + xx] = acc[m];
-  }
-}
-
-__global__ void __launch_bounds__(256) k_v3(const float* hg, const float* x, const float* y,
-                                            int64_t total, int n, int H, int W, Win w,
-                                            float w_ssim, float inv_m, float* grad) {
-  const int64_t HW = (int64_t)H * W;
-  const int strips = (H + RS - 1) / RS;
-  const int64_t items = (int64_t)n * strips * W;
-  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < items;
-       it += (int64_t)gridDim.x * blockDim.x) {
-    const int xx = (int)(it % W);
-    const int64_t cs = it / W;
-    const int y0 = (int)(cs % strips) * RS;
-    const int64_t cbase = (cs / strips) * HW;
-    float b[3][RS];
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int j = 0; j < RS; ++j) b[k][j] = 0.0f;
-#pragma unroll
-    for (int rr = 0; rr < RS + 2 * WR; ++rr) {
-      const int r = y0 - WR + rr;
-      if (r < 0 || r >= H) continue;
-      const int64_t o = cbase + (int64_t)r * W + xx;
-      float v[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) v[k] = hg[k * total + o];
-#pragma unroll
-      for (int j = 0; j < RS; ++j) {
-        const int i = rr - WR - j;
-        if (i < -WR || i > WR) continue;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) b[k][j] = fmaf(w.g[i + WR], v[k], b[k][j]);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < RS; ++j) {
-      if (y0 + j >= H) break;
-      const int64_t p = cbase + (int64_t)(y0 + j) * W + xx;
-      const float xv = x[p], yv = y[p];
-      const float d = xv - yv;
-      const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-      grad[p] = sgn * inv_m - w_ssim * inv_m * (b[0][j] + 2.f * xv * b[1][j] + yv * b[2][j]);
-    }
-  }
+  if ((tid & 31) == 0 && part != 0.0) atomicAdd(acc + b, part);
 }
 
 // L1 only: gradient and loss sum.
@@ -239,14 +276,12 @@ Win window() {
 
 }  // namespace
 
-size_t image_loss_scratch_bytes(int n, int H, int W) {
-  const size_t total = (size_t)n * H * W;
-  return 256 + ((sizeof(float) * 8 * total + 255) & ~(size_t)255);
-}
+size_t image_loss_scratch_bytes(int, int, int) { return 256; }
 
 cudaError_t launch_image_loss(const float* x, const float* y, int n, int H, int W,
                               float w_ssim, float* grad, double* acc, float* loss_out,
                               char* scratch, cudaStream_t s) {
+  (void)scratch;
   const int64_t total = (int64_t)n * H * W;
   if (total == 0) return cudaSuccess;
   const float inv_m = (float)(1.0 / (double)total);
@@ -255,19 +290,43 @@ cudaError_t launch_image_loss(const float* x, const float* y, int n, int H, int 
   if (w_ssim == 0.0f) {
     k_l1<<<grid_for(total), 256, 0, s>>>(x, y, total, inv_m, grad, acc);
   } else {
-    const Win w = window();
-    float* hm = reinterpret_cast<float*>(scratch + 256);  // [5][total], then [3][total]
-    float* G = hm + 5 * total;                             // [3][total]
-    const int64_t rows = (int64_t)n * H;
-    const int64_t segs = rows * ((W + HSEG - 1) / HSEG);
-    const unsigned hgrid = (unsigned)(segs < 148 * 16 ? segs : 148 * 16);
-    k_h5<<<hgrid, HSEG, 0, s>>>(x, y, rows, W, w, total, hm);
-    const int64_t strips = (int64_t)n * ((H + RS - 1) / RS) * W;
-    k_v5<<<grid_for(strips), 256, 0, s>>>(hm, x, y, total, n, H, W, w, w_ssim, G, acc);
-    k_h3<<<hgrid, HSEG, 0, s>>>(G, rows, W, w, total, hm);
-    k_v3<<<grid_for(strips), 256, 0, s>>>(hm, x, y, total, n, H, W, w, w_ssim, inv_m, grad);
+    SsimImages im;
+    im.B = 1;
+    im.dims = nullptr;
+    im.tile_off = nullptr;
+    im.pix_off = nullptr;
+    im.H = H;
+    im.W = W;
+    e = cudaFuncSetAttribute(k_ssim_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SSIM_SMEM);
+    if (e != cudaSuccess) return e;
+    const unsigned tiles = (unsigned)(((W + TO - 1) / TO) * ((H + TO - 1) / TO));
+    k_ssim_tile<<<tiles, SSIM_THREADS, SSIM_SMEM, s>>>(x, y, im, n, window(), w_ssim, grad,
+                                                       acc);
   }
   if (loss_out) k_loss_out<<<1, 32, 0, s>>>(acc, inv_m, loss_out);
+  return cudaGetLastError();
+}
+
+int ssim_tiles_of(int H, int W) { return ((W + TO - 1) / TO) * ((H + TO - 1) / TO); }
+
+cudaError_t launch_image_loss_batch(const float* x, const float* y, int B, const int4* dims,
+                                    const int* tile_off, const long long* pix_off, int tiles,
+                                    int n, float w_ssim, float* grad, double* acc,
+                                    cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(double) * B, s);
+  if (e != cudaSuccess || tiles == 0) return e;
+  SsimImages im;
+  im.B = B;
+  im.dims = dims;
+  im.tile_off = tile_off;
+  im.pix_off = pix_off;
+  im.H = im.W = 0;
+  e = cudaFuncSetAttribute(k_ssim_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)SSIM_SMEM);
+  if (e != cudaSuccess) return e;
+  k_ssim_tile<<<(unsigned)tiles, SSIM_THREADS, SSIM_SMEM, s>>>(x, y, im, n, window(), w_ssim,
+                                                               grad, acc);
   return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ def _pair(n, H, W, seed):
 
 
 @pytest.mark.parametrize("n,H,W,w", [(3, 64, 48, 0.1), (1, 37, 53, 1.0), (9, 32, 40, 0.1),
-                                     (3, 20, 20, 0.0), (2, 1, 30, 0.1)])
+                                     (3, 20, 20, 0.0), (2, 1, 30, 0.1), (3, 150, 97, 0.1)])
 def test_image_loss_and_gradient_match_oracle(n, H, W, w):
     x, y = _pair(n, H, W, 3 + n)
     g = torch.empty((n, H, W), device="cuda")
