@@ -45,11 +45,12 @@ SM_MAX_MHZ = 2032.0
 # (profiles/k_render_bwd_fit2048_rgb.md has the command)
 FUSED_TRAFFIC_2048_RGB = 62_268_416
 # library kernels of one fit step (the ncu launch list of the bench): finalize,
-# preprocess, 2 wide-Gaussian passes, 3 scan passes, emit, 2 segment sorts,
-# ranges, tile evaluations, fused adjoint, Adam
-KERNELS_PER_FIT_STEP = 14
-# the SSIM term adds the forward render and 4 image-loss passes
-SSIM_EXTRA_KERNELS = 5
+# preprocess, 2 wide-Gaussian passes, 3 scan passes (the last also writes the
+# tile ranges and the evaluation count), emit, 2 segment sorts, fused adjoint,
+# Adam
+KERNELS_PER_FIT_STEP = 12
+# the SSIM term adds the forward render and the one-pass image loss
+SSIM_EXTRA_KERNELS = 2
 
 
 def fused_kernel_ops(evals, pixels, K, n):

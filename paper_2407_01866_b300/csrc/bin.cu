@@ -6,6 +6,8 @@
 //                  (Eq. 2), radius 3*max(s); every exact tile hit increments
 //                  that tile's counter
 //   scan           exclusive prefix sum of the tile counters -> list offsets, M
+//                  (for one image its last pass also writes the tile ranges
+//                  and the evaluation count)
 //   k_emit         every hit takes a slot of its tile's segment (atomic cursor)
 //   k_segsort      a warp sorts a tile's segment by Gaussian index when it
 //                  is longer than the renderer's one-stage list
@@ -271,6 +273,49 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const In* in, Out* o
     if (i < n) out[i] = (Out)run;
     run += v[k];
   }
+}
+
+// Last pass of the tile-count scan of one image: the list offsets, and with
+// them each tile's [start, end) clipped to the stored intersections and the
+// evaluation count sum_j |S_j| * pixels(j) (k_ranges and k_tile_evals folded
+// in). M comes from the partials pass (status->m_needed).
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down_tiles(
+    const unsigned int* in, unsigned long long* out, int64_t n, const unsigned long long* part,
+    int2* range, int64_t m_cap, int H, int W, int tile, int tiles_x, DevStatus* st) {
+  __shared__ unsigned long long s_warp[33];
+  const int64_t base = (int64_t)blockIdx.x * SCAN_ITEMS + (int64_t)threadIdx.x * SCAN_PER_THREAD;
+  unsigned int v[SCAN_PER_THREAD];
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+    const int64_t i = base + k;
+    v[k] = i < n ? in[i] : 0u;
+    sum += v[k];
+  }
+  unsigned long long tot;
+  unsigned long long run = block_exclusive_scan<unsigned long long>(sum, s_warp, tot) +
+                           part[blockIdx.x];
+  const unsigned long long M = st->m_needed;
+  const unsigned long long live = M < (unsigned long long)m_cap ? M : (unsigned long long)m_cap;
+  unsigned long long evals = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+    const int64_t i = base + k;
+    if (i < n) {
+      out[i] = run;
+      const unsigned long long a = run < live ? run : live;
+      const unsigned long long b = run + v[k] < live ? run + v[k] : live;
+      range[i] = make_int2((int)a, (int)b);
+      const int tx = (int)(i % tiles_x), ty = (int)(i / tiles_x);
+      const int w = min((tx + 1) * tile, W) - tx * tile;
+      const int h = min((ty + 1) * tile, H) - ty * tile;
+      evals += (unsigned long long)v[k] * (unsigned long long)(w * h);
+    }
+    run += v[k];
+  }
+  unsigned long long etot;
+  block_exclusive_scan<unsigned long long>(evals, s_warp, etot);
+  if (threadIdx.x == 0 && etot) atomicAdd(&st->evals, etot);
 }
 
 template <typename In, typename Out>
@@ -596,15 +641,29 @@ cudaError_t run_binning(const PrepParams& p, int dtype, int T, unsigned long lon
   const bool batch = p.img_of != nullptr;
   if (batch) k_wide<true, true><<<148 * 4, 256, 0, s>>>(p);
   else k_wide<false, true><<<148 * 4, 256, 0, s>>>(p);
-  if ((e = launch_scan_u32_to_u64(p.tcnt, p.toff, T, part, &p.status->m_needed, s)) !=
-      cudaSuccess)
-    return e;
+  // the tile scan; for one image its last pass also writes the tile ranges
+  // and the evaluation count (the batch gets them from k_ranges and its own
+  // evaluation kernel after the emission)
+  if (batch) {
+    if ((e = launch_scan_u32_to_u64(p.tcnt, p.toff, T, part, &p.status->m_needed, s)) !=
+        cudaSuccess)
+      return e;
+  } else if (T > 0) {
+    const int64_t nb = ((int64_t)T + SCAN_ITEMS - 1) / SCAN_ITEMS;
+    k_scan_reduce<unsigned int, unsigned long long><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(
+        p.tcnt, T, part);
+    k_scan_partials<<<1, 1024, 0, s>>>(part, nb, &p.status->m_needed);
+    k_scan_down_tiles<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(p.tcnt, p.toff, T, part, range,
+                                                            p.m_cap, p.H, p.W, p.tile,
+                                                            p.tiles_x, p.status);
+  }
   if ((e = launch_emit(p, s)) != cudaSuccess) return e;
   if (batch) k_wide<true, false><<<148 * 4, 256, 0, s>>>(p);
   else k_wide<false, false><<<148 * 4, 256, 0, s>>>(p);
   if ((e = launch_segsort(p.vals, p.tmp, p.toff, T, p.status, p.m_cap, p.big, sort_min, s)) !=
       cudaSuccess)
     return e;
+  if (!batch) return cudaGetLastError();
   return launch_ranges(p.toff, range, T, p.m_cap, p.H, p.W, p.tile,
                        p.img_of ? 0 : p.tiles_x, p.status, s);
 }
