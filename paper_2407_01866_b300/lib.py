@@ -420,32 +420,60 @@ class Binner:
         return bins
 
 
+# Binners of the autograd path, one per (shape, config, device): their
+# workspaces are allocated once and reused by every call of that shape.
+_BINNERS = {}
+
+
+def _binner_for(N, n, H, W, cfg, device):
+    key = (N, n, H, W, cfg.K, cfg.tile, cfg.normalize, device.index)
+    b = _BINNERS.get(key)
+    if b is None:
+        with torch.cuda.device(device):
+            b = _BINNERS[key] = Binner(N, n, H, W, cfg)
+    return b
+
+
 class _RenderFn(torch.autograd.Function):
+    """Forward render and its adjoint. The binning workspace is cached per
+    shape; the backward bins the saved parameters again (into that cached
+    workspace), so interleaved forwards of the same shape cannot disturb it.
+    With check=False no call synchronises the host and an intersection
+    overflow goes undetected (that call's lists are truncated): make a first
+    checked call of the shape to size the cached workspace."""
+
     @staticmethod
-    def forward(ctx, xy, theta, inv_scale, color, H, W, cfg):
+    def forward(ctx, xy, theta, inv_scale, color, H, W, cfg, check):
         g = gaussians_view(xy, theta, inv_scale, color)
-        binner = Binner(g.N, g.n, H, W, cfg)
-        bins = binner.bin(g)
+        binner = _binner_for(g.N, g.n, H, W, cfg, xy.device)
+        bins = binner.bin(g, check=check)
         img = torch.empty((g.n, H, W), dtype=torch.float32, device=xy.device)
         render_forward(bins, cfg, img)
         ctx.save_for_backward(xy, theta, inv_scale, color)
-        ctx.keep = (binner, bins, cfg, H, W)
+        ctx.keep = (cfg, H, W, check)
         return img
 
     @staticmethod
     def backward(ctx, grad_img):
         xy, theta, inv_scale, color = ctx.saved_tensors
-        binner, bins, cfg, H, W = ctx.keep
+        cfg, H, W, check = ctx.keep
         g = gaussians_view(xy, theta, inv_scale, color)
+        binner = _binner_for(g.N, g.n, H, W, cfg, xy.device)
+        bins = binner.bin(g, check=check)
         n = color.shape[1]
         grad = torch.empty((xy.shape[0], 5 + n), dtype=torch.float32, device=xy.device)
         render_backward(g, bins, cfg, grad_img.contiguous().float(), None, grad)
-        return (grad[:, 0:2], grad[:, 2], grad[:, 3:5], grad[:, 5:], None, None, None)
+        return (grad[:, 0:2], grad[:, 2], grad[:, 3:5], grad[:, 5:], None, None, None, None)
 
 
-def render(xy, theta, inv_scale, color, H, W, cfg=None):
-    """Differentiable render (Eq. 5) -> planar float32 [n, H, W]."""
-    return _RenderFn.apply(xy, theta, inv_scale, color, H, W, cfg or default_config())
+def render(xy, theta, inv_scale, color, H, W, cfg=None, check=True):
+    """Differentiable render (Eq. 5) -> planar float32 [n, H, W].
+
+    check=True (default) synchronises once per call to re-bin with a larger
+    capacity if the intersections overflowed; check=False keeps every call
+    stream-ordered (graph-capturable after a first checked call has sized
+    the cached workspace)."""
+    return _RenderFn.apply(xy, theta, inv_scale, color, H, W, cfg or default_config(), check)
 
 
 class Fitter:

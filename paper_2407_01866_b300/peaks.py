@@ -36,3 +36,19 @@ def probe(kind, iters=2000, reps=5):
     if rc != 0:
         raise RuntimeError(f"igs_peak_probe({kind}) failed with {rc}")
     return o.value, i.value, ms.value
+
+
+def main():
+    """Prints every probe's rates on the current device as one JSON line:
+    python -m paper_2407_01866_b300.peaks"""
+    import json
+    out = {}
+    for kind in KINDS:
+        iters = 200 if kind == "match" else 2000
+        ops, inst, ms = probe(kind, iters=iters, reps=5)
+        out[kind] = {"lane_ops_per_s": ops, "instructions_per_s": inst, "best_ms": ms}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

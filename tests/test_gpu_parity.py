@@ -289,3 +289,29 @@ def test_autograd_render_matches_oracle_forward_and_adjoint():
     want = O.backward_image(g, weight, H, W)
     errs = grad_rel_error(got.astype(np.float64), want)
     assert max(errs.values()) <= GRAD_TOL, errs
+
+
+def test_autograd_render_reuses_its_workspace_and_runs_unchecked():
+    """Repeated renders of one shape reuse a cached workspace (no allocation
+    per call); check=False renders with no host synchronisation, and two
+    interleaved forwards of the same shape keep their own adjoints."""
+    H, W, N, n = 48, 40, 250, 3
+    sets = [oset(N, n, 30 + k) for k in range(2)]
+    tss = [[torch.from_numpy(a.copy()).cuda().requires_grad_(True)
+            for a in (g.xy, g.theta, g.inv_scale, g.color)] for g in sets]
+    L.render(*tss[0], H, W)   # a checked call sizes the cached workspace
+    before = len(L._BINNERS)
+    imgs = [L.render(*ts, H, W, check=False) for ts in tss]
+    assert len(L._BINNERS) == before
+    weight = np.random.default_rng(23).standard_normal((n, H, W)).astype(np.float32)
+    wt = torch.from_numpy(weight).cuda()
+    for g, ts, img in zip(sets, tss, imgs):
+        np.testing.assert_allclose(img.detach().cpu().numpy(), O.render_image(g, H, W),
+                                   rtol=0, atol=PIX_TOL)
+    (imgs[0] * wt).sum().backward()
+    (imgs[1] * wt).sum().backward()
+    for g, ts in zip(sets, tss):
+        got = np.concatenate([ts[0].grad.cpu().numpy(), ts[1].grad.cpu().numpy()[:, None],
+                              ts[2].grad.cpu().numpy(), ts[3].grad.cpu().numpy()], axis=1)
+        errs = grad_rel_error(got.astype(np.float64), O.backward_image(g, weight, H, W))
+        assert max(errs.values()) <= GRAD_TOL, errs
