@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():
     pytest.skip("no CUDA device", allow_module_level=True)
 
-from gpu_harness import GpuSet, grad_rel_error  # noqa: E402
+from gpu_harness import GpuSet, grad_elem_rel_error, grad_rel_error  # noqa: E402
 
 PIX_TOL = 1e-5
 GRAD_TOL = 1e-3
@@ -69,6 +69,7 @@ def test_forward_matches_oracle(case):
     got = gs.forward()
     want = O.render_image(g, H, W, K=K, tile=tile)
     err = np.abs(got - want).max()
+    print(f"forward {H}x{W} N={N} n={n} K={K} tile={tile}: max |pixel - oracle| {err:.2e}")
     assert err <= PIX_TOL, err
 
 
@@ -108,6 +109,9 @@ def test_fused_l1_loss_and_gradient_match_oracle(case):
     want = O.backward_image(g, dimg, H, W, K=K, tile=tile)
     assert abs(st.loss_sum / (H * W * n) - loss) <= 1e-6
     errs = grad_rel_error(got, want)
+    print(f"fused L1 {H}x{W} N={N} n={n}: loss {st.loss_sum / (H * W * n):.8f} vs {loss:.8f}, "
+          f"gradient normwise {max(errs.values()):.2e}, per element "
+          f"{max(grad_elem_rel_error(got, want).values()):.2e}")
     assert max(errs.values()) <= GRAD_TOL, errs
 
 
