@@ -44,6 +44,7 @@ SM_MAX_MHZ = 2032.0
 # dram__bytes_read.sum 61,395,968 + dram__bytes_write.sum 872,448
 # (profiles/k_render_bwd_fit2048_rgb.md has the command)
 FUSED_TRAFFIC_2048_RGB = 62_268_416
+TRAFFIC_STEPS_MAX = 50
 # library kernels of one fit step (the ncu launch list of the bench): finalize,
 # preprocess, 2 wide-Gaussian passes, 3 scan passes (the last also writes the
 # tile ranges and the evaluation count), emit, 2 segment sorts, fused adjoint,
@@ -73,7 +74,7 @@ def fused_kernel_mufu(pixels, K):
 class ClockSampler:
     """Samples the SM clock and the throttle reasons while running: through
     NVML (every 20 ms) where the library is present, else nvidia-smi (every
-    200 ms). Read-only queries."""
+    50 ms plus the query's own time). Read-only queries."""
 
     REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -122,7 +123,7 @@ class ClockSampler:
                 self._sample_nvml() if self._nvml else self._sample_smi()
             except Exception:
                 pass
-            self._stop.wait(0.02 if self._nvml else 0.2)
+            self._stop.wait(0.02 if self._nvml else 0.05)
 
     def __enter__(self):
         self._t = threading.Thread(target=self._run, daemon=True)
@@ -470,8 +471,12 @@ def run_ours(args, w=WORKLOAD):
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": fp32_peak / 1e12,
                          "unit": "T fp32 lane-ops/s", "frac": achieved / fp32_peak,
                          "traffic": (FUSED_TRAFFIC_2048_RGB
-                                     if w["name"] == "fit2048_rgb" and half is None else None),
+                                     if w["name"] == "fit2048_rgb" and half is None
+                                     and args.steps <= TRAFFIC_STEPS_MAX else None),
                          "traffic_unit": "bytes per launch",
+                         "traffic_state": ("ncu DRAM read + write of this kernel after 20 fit "
+                                           "steps from the initial parameters; reported for "
+                                           f"runs of at most {TRAFFIC_STEPS_MAX} steps"),
                          "kernel": "k_render_bwd (fused forward + L1 + adjoint)",
                          "kernel_ms": k_ms, "ops_per_launch": ops,
                          "peak_note": "measured on this GPU in this run (libigs_peaks: chains of "
