@@ -496,7 +496,7 @@ def run_ours(args, w=WORKLOAD):
                     "h2d_bytes_per_step": int(target.numel() * 4), "d2h_bytes_per_step": 4},
             "clocks": clocks.summary(),
         }
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:   # the oracle baseline runs at N = 1 only
             line["cpu_baseline"] = cpu_baseline(target_np, P_np, budget_s=args.cpu_budget, w=w)
         print(json.dumps(line))
     if dist:

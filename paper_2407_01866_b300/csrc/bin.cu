@@ -42,6 +42,8 @@ __device__ __forceinline__ void tile_span(float m, float r, int tile, int tiles,
 // A Gaussian whose tile box has more tiles than this is binned by a whole CTA
 // (threads stride over the box) instead of one thread.
 constexpr int WIDE_TILES = 64;
+// CTAs of the wide-Gaussian passes (they stride over the wide Gaussians)
+constexpr int WIDE_GRID = 148 * 16;
 
 // Image geometry of Gaussian i: the single image, or its image in a batch.
 struct ImgGeo {
@@ -639,8 +641,10 @@ cudaError_t run_binning(const PrepParams& p, int dtype, int T, unsigned long lon
   if (e != cudaSuccess) return e;
   if ((e = launch_preprocess(p, dtype, s)) != cudaSuccess) return e;
   const bool batch = p.img_of != nullptr;
-  if (batch) k_wide<true, true><<<148 * 4, 256, 0, s>>>(p);
-  else k_wide<false, true><<<148 * 4, 256, 0, s>>>(p);
+  // one CTA per wide Gaussian (up to WIDE_GRID at a time): their hits take
+  // returning atomics, so many boxes must be in flight at once
+  if (batch) k_wide<true, true><<<WIDE_GRID, 256, 0, s>>>(p);
+  else k_wide<false, true><<<WIDE_GRID, 256, 0, s>>>(p);
   // the tile scan; for one image its last pass also writes the tile ranges
   // and the evaluation count (the batch gets them from k_ranges and its own
   // evaluation kernel after the emission)
@@ -658,8 +662,8 @@ cudaError_t run_binning(const PrepParams& p, int dtype, int T, unsigned long lon
                                                             p.tiles_x, p.status);
   }
   if ((e = launch_emit(p, s)) != cudaSuccess) return e;
-  if (batch) k_wide<true, false><<<148 * 4, 256, 0, s>>>(p);
-  else k_wide<false, false><<<148 * 4, 256, 0, s>>>(p);
+  if (batch) k_wide<true, false><<<WIDE_GRID, 256, 0, s>>>(p);
+  else k_wide<false, false><<<WIDE_GRID, 256, 0, s>>>(p);
   if ((e = launch_segsort(p.vals, p.tmp, p.toff, T, p.status, p.m_cap, p.big, sort_min, s)) !=
       cudaSuccess)
     return e;

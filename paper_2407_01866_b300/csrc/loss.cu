@@ -159,9 +159,9 @@ __global__ void __launch_bounds__(SSIM_THREADS) k_ssim_tile(const float* x, cons
           const float B1 = mx * mx + my * my + C1, B2 = vx + vy + C2;
           const float iB = 1.f / (B1 * B2);
           const float S = A1 * A2 * iB;
-          const float dS_dvx = -S / B2;
+          const float dS_dvx = -S * (B1 * iB);   // -S / B2
           const float dS_dcxy = 2.f * A1 * iB;
-          const float dmx = 2.f * my * A2 * iB - S * 2.f * mx / B1;
+          const float dmx = 2.f * my * A2 * iB - S * 2.f * mx * (B2 * iB);  // ... / B1
           g1 = dmx - 2.f * mx * dS_dvx - my * dS_dcxy;
           g2 = dS_dvx;
           g3 = dS_dcxy;
