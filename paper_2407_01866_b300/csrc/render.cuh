@@ -83,6 +83,14 @@ __device__ __forceinline__ float4 block_rect(int x0, int y0) {
 constexpr float F_INF = __builtin_huge_valf();
 constexpr int GID_NONE = 0x7fffffff;  // tie cut-off that admits every index
 
+// Reciprocal on the MUFU (rcp.approx: within one ulp).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+
 // Staged candidate record in shared memory:
 //   a = (mx, my, A00, B)   geometry of the ranking key
 //   b = (A11, index as int bits)
@@ -354,6 +362,7 @@ struct PixelBlend {
   float cr[NCR];    // blended colour
   float tau;        // K-th key (+inf if |S_j| < K)
   float q0;         // smallest key (0 when unnormalised)
+  float iz;         // 1 / Z (normalised, Z > 0), 1 (unnormalised) or 0
   int gcut;         // largest index admitted among winners whose key equals tau
   int nw;           // winners recorded by pass B for pass C (fast path adjoint)
 };
@@ -438,9 +447,9 @@ __device__ __forceinline__ void blend_pass(const RenderParams& p, int2 range, fl
       }
     }
   }
-  const float iz = p.normalize ? (r.Z > 0.0f ? 1.0f / r.Z : 0.0f) : 1.0f;
+  r.iz = p.normalize ? (r.Z > 0.0f ? rcp_approx(r.Z) : 0.0f) : 1.0f;
 #pragma unroll
-  for (int c = 0; c < NCR; ++c) r.cr[c] *= iz;
+  for (int c = 0; c < NCR; ++c) r.cr[c] *= r.iz;
 }
 
 // ---------------------------------------------------------------------------
@@ -621,9 +630,9 @@ __device__ __forceinline__ void culled_blend(const RenderParams& p, int cnt, flo
       if (two) take(j1, q1, __float_as_int(b1.y));
     }
   }
-  const float iz = p.normalize ? (r.Z > 0.0f ? 1.0f / r.Z : 0.0f) : 1.0f;
+  r.iz = p.normalize ? (r.Z > 0.0f ? rcp_approx(r.Z) : 0.0f) : 1.0f;
 #pragma unroll
-  for (int c = 0; c < NCR; ++c) r.cr[c] *= iz;
+  for (int c = 0; c < NCR; ++c) r.cr[c] *= r.iz;
 }
 
 // ---------------------------------------------------------------------------
@@ -693,10 +702,18 @@ __device__ __forceinline__ void packed_keys(int cnt, float px, float py, bool li
                                             int& mdrop) {
   const int lane = threadIdx.x & 31;
   // the first K candidates (nearest first) fill the top K through a network
+  if (cnt >= K) {
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const float4 a = s_a[k];
-    tq[k] = k < cnt ? pack_key(rank_key(px, py, a.x, a.y, a.z, a.w, s_b[k].x), k) : PK_NONE;
+    for (int k = 0; k < K; ++k) {
+      const float4 a = s_a[k];
+      tq[k] = pack_key(rank_key(px, py, a.x, a.y, a.z, a.w, s_b[k].x), k);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const float4 a = s_a[k];
+      tq[k] = k < cnt ? pack_key(rank_key(px, py, a.x, a.y, a.z, a.w, s_b[k].x), k) : PK_NONE;
+    }
   }
   sort_network_pk<K>(tq);
   mdrop = PK_NONE;
@@ -780,24 +797,30 @@ __device__ __forceinline__ void exact_winners(const RenderParams& p, int cnt, fl
 
 // Eq. 5 over the winners whose slots are in tq: their keys are recomputed
 // exactly, q_min is the smallest of them, and the winners are blended in the
-// packed order. all_valid: every entry of tq holds a winner (lists of at
-// least K entries).
-template <int K, int NC, int CH>
+// packed order with w = exp(-(q - q_min)/2). ALL: every entry of tq holds a
+// winner (lists of at least K entries), so no entry is tested. REC: each
+// winner of a live pixel also sets the lane's bit in its warp's mask of the
+// slot (cnt_w), for pass C's records.
+template <int K, int NC, int CH, bool ALL, bool REC>
 __device__ __forceinline__ void blend_winners(const RenderParams& p, float px, float py,
-                                              const int (&tq)[K], bool all_valid,
+                                              const int (&tq)[K], bool live,
                                               const float4* s_a, const float2* s_b,
-                                              const float* s_col, PixelBlend<Chan<NC>::R>& r) {
+                                              const float* s_col, unsigned* cnt_w,
+                                              PixelBlend<Chan<NC>::R>& r) {
   constexpr int NCR = Chan<NC>::R;
   const int n = nchan<NC>(p);
+  const unsigned bit = 1u << (threadIdx.x & 31);
   float qe[K];
   float q0 = F_INF;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const bool ok = all_valid || tq[k] != PK_NONE;
-    const int j = ok ? (tq[k] & 0xff) : 0;
-    const float4 a = s_a[j];
-    qe[k] = ok ? rank_key(px, py, a.x, a.y, a.z, a.w, s_b[j].x) : F_INF;
-    q0 = fminf(q0, qe[k]);
+    if (ALL || tq[k] != PK_NONE) {
+      const int j = tq[k] & 0xff;
+      if (REC && live) atomicOr(&cnt_w[j], bit);
+      const float4 a = s_a[j];
+      qe[k] = rank_key(px, py, a.x, a.y, a.z, a.w, s_b[j].x);
+      q0 = fminf(q0, qe[k]);
+    }
   }
   r.q0 = p.normalize ? q0 : 0.0f;
   r.Z = 0.0f;
@@ -805,7 +828,7 @@ __device__ __forceinline__ void blend_winners(const RenderParams& p, float px, f
   for (int c = 0; c < NCR; ++c) r.cr[c] = 0.0f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    if (all_valid || tq[k] != PK_NONE) {
+    if (ALL || tq[k] != PK_NONE) {
       const float w = blend_weight(r.q0, qe[k]);  // exactly 1 at q = q_min
       r.Z += w;
       float cc[NCR];
@@ -815,37 +838,21 @@ __device__ __forceinline__ void blend_winners(const RenderParams& p, float px, f
         if (NC > 0 || c < n) r.cr[c] = fmaf(w, cc[c], r.cr[c]);
     }
   }
-  const float iz = p.normalize ? (r.Z > 0.0f ? 1.0f / r.Z : 0.0f) : 1.0f;
+  r.iz = p.normalize ? (r.Z > 0.0f ? rcp_approx(r.Z) : 0.0f) : 1.0f;
 #pragma unroll
-  for (int c = 0; c < NCR; ++c) r.cr[c] *= iz;
+  for (int c = 0; c < NCR; ++c) r.cr[c] *= r.iz;
   r.tau = F_INF;
   r.gcut = GID_NONE;
 }
 
-// Records, for pass C, the winners of every live pixel of the warp. Each
-// pixel sets its bit in the warp's mask of every slot it won (cnt_w[slot],
-// zeroed before); then its k-th winner goes to wrec[k * NT] as (slot << 5 |
-// number of lower lanes that won the slot). The number of a slot's winning
-// pixels in the warp is the popcount of its mask. Returns the records made.
-template <int K, int NT>
-__device__ __forceinline__ int record_winners(const int (&tq)[K], bool live, unsigned* cnt_w,
-                                              unsigned short* wrec) {
-  const int lane = threadIdx.x & 31;
-  const unsigned bit = 1u << lane;
-#pragma unroll
-  for (int k = 0; k < K; ++k)
-    if (live && tq[k] != PK_NONE) atomicOr(&cnt_w[tq[k] & 0xff], bit);
-  __syncwarp();
-  int nw = 0;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (live && tq[k] != PK_NONE) {
-      const int j = tq[k] & 0xff;
-      wrec[k * NT] = (unsigned short)((j << 5) | __popc(cnt_w[j] & (bit - 1u)));
-      ++nw;
-    }
-  }
-  return nw;
+// Pass C's record of the k-th winner of a live pixel, once every lane of the
+// warp has set its bits (cnt_w): (slot << 5) | number of lower lanes that won
+// the slot; the number of the slot's winning pixels in the warp is the
+// popcount of its mask.
+__device__ __forceinline__ int winner_record(int pk, const unsigned* cnt_w) {
+  const int j = pk & 0xff;
+  const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+  return (j << 5) | __popc(cnt_w[j] & lt);
 }
 
 // Where one tile of one image lives (the batched form renders many images).
@@ -883,7 +890,11 @@ __device__ __forceinline__ void fwd_tile(const RenderParams& p, const TileCtx& t
       packed_keys<K>(len, px, py, in_img, R, s_a, s_b, s_e, tk, md);
       if (__any_sync(FULL_MASK, in_img && pk_ambiguous(tk[K - 1], md)))
         exact_winners<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tk);
-      blend_winners<K, NC, NT>(p, px, py, tk, len >= K, s_a, s_b, s_col, r);
+      if (len >= K)
+        blend_winners<K, NC, NT, true, false>(p, px, py, tk, in_img, s_a, s_b, s_col, nullptr, r);
+      else
+        blend_winners<K, NC, NT, false, false>(p, px, py, tk, in_img, s_a, s_b, s_col, nullptr,
+                                               r);
     } else {
       float mdrop;
       culled_keys<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tq, mdrop);
@@ -945,8 +956,8 @@ __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   // words per candidate, as np >= 6 and CH <= NT, so they end inside slot_b)
   L.slot_a = o; o = al4(o + np * CH);
   L.slot_b = o; o = al4(o + np * NT);     // pass C per-thread sums B_t; rank keys before
-  // pass B's 16-bit winner records, then pass C's pair table (<= 16 NT
-  // entries each); the chunked path's (tau, cut-off) per pixel
+  // pass C's table of 16-bit (candidate, pixel) pairs (<= 16 NT entries);
+  // the chunked path's (tau, cut-off) per pixel
   L.win = o;    o += 8 * NT;
   L.coff = o;   o += CH + 1;              // first pair of every candidate
   L.loss = o;   o += NWB;               // per-warp loss partials
@@ -1042,11 +1053,11 @@ __device__ __forceinline__ int div_small(int a, int d, float inv) {
 
 // Pass C of the fast path. The winning (candidate, pixel) pairs, in
 // (candidate, warp block, pixel) order, are first written out as a table of
-// 16-bit entries (candidate << 8 | pixel) by a counting sort of pass B's
-// records: a scan over candidates of their per-warp-block counts gives every
-// (candidate, warp block) its first slot, and each pixel stores its own
-// winners at that slot plus its rank (the records are read into registers
-// before the scan's barriers, as the table overwrites them). The table is split into equal contiguous ranges, one per thread; a thread
+// 16-bit entries (candidate << 8 | pixel) by a counting sort of the winner
+// records (ew, in each pixel's registers): a scan over candidates of their
+// per-warp-block counts gives every (candidate, warp block) its first slot,
+// and each pixel stores its own winners at that slot plus its rank. The
+// table is split into equal contiguous ranges, one per thread; a thread
 // accumulates the candidates of its range in registers. A candidate's partial
 // sums go to the candidate's slot A_j, written by the one thread whose range
 // holds the candidate's first pair, or, for the candidate a range opens with
@@ -1056,7 +1067,8 @@ __device__ __forceinline__ int div_small(int a, int d, float inv) {
 // Needs at most NT * 16 pairs (K <= 16): s_win / s_pair hold 16 NT entries.
 template <int TILE, int K, int NC, int CH>
 __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx& t, int cnt,
-                                            int nw, const float4* s_a, const float2* s_b,
+                                            int nw, const int (&ew)[KS<K>::A],
+                                            const float4* s_a, const float2* s_b,
                                             const float* s_col, unsigned short* s_win,
                                             unsigned* s_cnt, const float4* s_ps0,
                                             const float* s_gh, float* s_slot_a, float* s_slot_b,
@@ -1067,10 +1079,7 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
   constexpr int A = KS<K>::A;
   const int n = nchan<NC>(p);
   const int tid = threadIdx.x;
-  // this pixel's records, and candidate tid's counts per warp block
-  unsigned short ew[A];
-#pragma unroll
-  for (int k = 0; k < A; ++k) ew[k] = k < nw ? s_win[k * NT + tid] : (unsigned short)0;
+  // candidate tid's counts per warp block
   int pre[NWB];
   int tot = 0;
 #pragma unroll
@@ -1079,7 +1088,7 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
     if (tid < cnt) tot += __popc(s_cnt[wb * CH + tid]);
   }
   int P;
-  const int base = block_scan_int(tid < cnt ? tot : 0, s_scan, P);  // ends every read of s_win
+  const int base = block_scan_int(tid < cnt ? tot : 0, s_scan, P);
   if (tid < cnt) {
 #pragma unroll
     for (int wb = 0; wb < NWB; ++wb) s_cnt[wb * CH + tid] = (unsigned)(base + pre[wb]);
@@ -1314,7 +1323,7 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   float* s_slot_b = smem + SL.slot_b;
   float2* s_e = reinterpret_cast<float2*>(s_slot_a);      // until pass C
   unsigned* s_key = reinterpret_cast<unsigned*>(s_slot_b);  // while staging
-  // pass B's per-pixel records, then pass C's pair table (fast path)
+  // pass C's pair table (fast path)
   unsigned short* s_win = reinterpret_cast<unsigned short*>(smem + SL.win);
   float2* s_ps1 = reinterpret_cast<float2*>(smem + SL.win);  // chunked path only
   // per (warp block, candidate) counts of pass B, then first pair slots; after
@@ -1340,6 +1349,7 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   const int len = t.range.y - t.range.x;
   const bool fast = len <= CH;
   float tq[KS<K>::A];
+  int ew[KS<K>::A];  // fast path: this pixel's winner records for pass C
   PixelBlend<NCR> r;
   __syncthreads();  // the previous tile of a persistent CTA is done with smem
   if (fast) {
@@ -1355,8 +1365,19 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
       packed_keys<K>(len, px, py, in_img, R, s_a, s_b, s_e, tk, md);
       if (__any_sync(FULL_MASK, in_img && pk_ambiguous(tk[K - 1], md)))
         exact_winners<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tk);
-      blend_winners<K, NC, CH>(p, px, py, tk, len >= K, s_a, s_b, s_col, r);
-      r.nw = record_winners<K, NT>(tk, in_img, cnt_w, s_win + threadIdx.x);
+      if (len >= K)
+        blend_winners<K, NC, CH, true, true>(p, px, py, tk, in_img, s_a, s_b, s_col, cnt_w, r);
+      else
+        blend_winners<K, NC, CH, false, true>(p, px, py, tk, in_img, s_a, s_b, s_col, cnt_w, r);
+      __syncwarp();
+      // winners in ascending packed order: PK_NONE entries come last
+      r.nw = 0;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const bool ok = in_img && tk[k] != PK_NONE;
+        ew[k] = ok ? winner_record(tk[k], cnt_w) : 0;
+        r.nw += ok ? 1 : 0;
+      }
     } else {
       float mdrop;
       culled_keys<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tq, mdrop);
@@ -1371,7 +1392,7 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   float loss = 0.0f;
   const bool live = in_img && r.Z > 0.0f;
   float beta = 0.0f;
-  const float iz = live ? (p.normalize ? 1.0f / r.Z : 1.0f) : 0.0f;
+  const float iz = live ? r.iz : 0.0f;
 #pragma unroll
   for (int c = 0; c < NCR; ++c) {
     if (NC > 0 || c < n) {
@@ -1412,7 +1433,7 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
 
   // ---- pass C: candidate-major accumulation of the adjoint
   if (flat) {
-    flat_pass_c<TILE, K, NC, CH>(p, t, len, r.nw, s_a, s_b, s_col, s_win, s_cnt, s_ps0, s_gh,
+    flat_pass_c<TILE, K, NC, CH>(p, t, len, r.nw, ew, s_a, s_b, s_col, s_win, s_cnt, s_ps0, s_gh,
                                  s_slot_a, s_slot_b, reinterpret_cast<int*>(smem + SL.coff),
                                  reinterpret_cast<int*>(smem + SL.scan));
   } else {
