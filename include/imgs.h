@@ -159,7 +159,9 @@ void igs_default_config(igs_config* cfg);
 
 /* Bytes of device workspace that igs_preprocess_bin needs for N Gaussians
  * with n channels on an H x W image and room for m_capacity tile-Gaussian
- * intersections. Host only; no CUDA call. */
+ * intersections. Host only; no CUDA call. H and W are 1..2^20, with at most
+ * 65535 rows of tiles (the render grid's y extent); IGS_ERR_INVALID_ARG
+ * otherwise, here and in igs_preprocess_bin. */
 int igs_workspace_size(int64_t N, int32_t n, int32_t H, int32_t W,
                        const igs_config* cfg, int64_t m_capacity, size_t* bytes);
 

@@ -87,9 +87,14 @@ static int check_config(const igs_config* cfg, int n) {
   return IGS_OK;
 }
 
-static int check_image(int H, int W) {
+static int check_image(int H, int W, int tile) {
   if (H <= 0 || W <= 0 || H > (1 << 20) || W > (1 << 20))
     return fail(IGS_ERR_INVALID_ARG, "bad image size %d x %d", H, W);
+  // the render grid has one CTA per tile, (tiles_x, tiles_y), and a grid's
+  // y extent is at most 65535
+  if ((H + tile - 1) / tile > 65535)
+    return fail(IGS_ERR_INVALID_ARG, "image height %d needs more than 65535 rows of %d-px tiles",
+                H, tile);
   return IGS_OK;
 }
 
@@ -219,7 +224,7 @@ int igs_workspace_size(int64_t N, int32_t n, int32_t H, int32_t W, const igs_con
                        int64_t m_capacity, size_t* bytes) {
   if (!bytes) return fail(IGS_ERR_INVALID_ARG, "bytes is NULL");
   if (int r = check_config(cfg, n)) return r;
-  if (int r = check_image(H, W)) return r;
+  if (int r = check_image(H, W, cfg->tile)) return r;
   if (N < 0 || m_capacity < 1 || m_capacity > (int64_t)INT32_MAX)
     return fail(IGS_ERR_INVALID_ARG, "N or m_capacity out of range");
   *bytes = ws_layout(N, n, H, W, cfg->tile, m_capacity).total + fit_extra_bytes(cfg, n, H, W);
@@ -231,7 +236,7 @@ int igs_preprocess_bin(const igs_gaussians* g, int32_t H, int32_t W, const igs_c
                        igs_stream stream) {
   if (int r = check_gaussians(g)) return r;
   if (int r = check_config(cfg, g->n)) return r;
-  if (int r = check_image(H, W)) return r;
+  if (int r = check_image(H, W, cfg->tile)) return r;
   if (!out) return fail(IGS_ERR_INVALID_ARG, "out is NULL");
   if (!ws) return fail(IGS_ERR_INVALID_ARG, "workspace is NULL");
   if (!aligned(ws, 256)) return fail(IGS_ERR_ALIGN, "workspace must be 256-byte aligned");

@@ -240,7 +240,7 @@ __device__ __forceinline__ void stage_sorted(const RenderParams& p, int base, in
     if (gid >= 0) {
       s_a[r] = ga;
       s_b[r] = make_float2(ga11, __int_as_float(gid));
-      s_e[r] = make_float2(0.5f / ga.z, 0.5f / ga11);
+      s_e[r] = make_float2(0.5f * rcp_approx(ga.z), 0.5f * rcp_approx(ga11));
       if (NC > 0) {
 #pragma unroll
         for (int c = 0; c < NCS; ++c) s_col[r * col_stride(NC) + c] = col[c];
@@ -722,15 +722,12 @@ __device__ __forceinline__ void packed_keys(int cnt, float px, float py, bool li
     const int jl = c0 + lane;
     const float bnd = jl < cnt ? key_lower_bound(s_a[jl], s_b[jl].x, s_e[jl], R) : F_INF;
     unsigned m = __ballot_sync(FULL_MASK, !(bnd > thr));
+    // a lane whose key is not better passes it through the network
+    // unchanged (it is at least every kept key) and drops it
     auto take = [&](int pk) {
-      const bool better = pk < tq[K - 1];
-      int out = pk;
-      if (__any_sync(FULL_MASK, better)) {
-        int x = better ? pk : PK_NONE;
-        insert_pk<K>(tq, x);
-        out = better ? x : pk;
-      }
-      mdrop = min(mdrop, out);
+      int x = pk;
+      if (__any_sync(FULL_MASK, pk < tq[K - 1])) insert_pk<K>(tq, x);
+      mdrop = min(mdrop, x);
     };
     while (m) {
       const int j0 = c0 + __ffs(m) - 1;
@@ -855,6 +852,21 @@ __device__ __forceinline__ int winner_record(int pk, const unsigned* cnt_w) {
   return (j << 5) | __popc(cnt_w[j] & lt);
 }
 
+// A pixel's winner records for pass C, in registers: one per register, or
+// (PACK, where registers are scarcer) two 16-bit records per register.
+template <int A, bool PACK>
+struct WinRecs {
+  int v[PACK ? (A + 1) / 2 : A];
+  __device__ __forceinline__ void set(int k, int rec) {
+    if (!PACK) v[k] = rec;
+    else if (k & 1) v[k >> 1] |= rec << 16;
+    else v[k >> 1] = rec;
+  }
+  __device__ __forceinline__ unsigned get(int k) const {
+    return PACK ? (((unsigned)v[k >> 1] >> ((k & 1) * 16)) & 0xffffu) : (unsigned)v[k];
+  }
+};
+
 // Where one tile of one image lives (the batched form renders many images).
 struct TileCtx {
   int2 range;        // [start, end) of the tile's list
@@ -922,11 +934,11 @@ __global__ void __launch_bounds__(TILE * TILE, TILE == 16 ? 6 : 16) k_render_fwd
   __shared__ float2 s_e[NT];
   __shared__ __align__(16) unsigned s_key[2 * NT];
   __shared__ __align__(16) float s_col[NT * col_stride(NC)];
-  const int tile_id = blockIdx.x;
+  const int tile_id = blockIdx.y * p.tiles_x + blockIdx.x;  // grid (tiles_x, tiles_y)
   TileCtx t;
   t.range = p.range[tile_id];
-  t.x0 = (tile_id % p.tiles_x) * TILE;
-  t.y0 = (tile_id / p.tiles_x) * TILE;
+  t.x0 = blockIdx.x * TILE;
+  t.y0 = blockIdx.y * TILE;
   t.H = p.H;
   t.W = p.W;
   t.off = 0;
@@ -1013,6 +1025,10 @@ __device__ __forceinline__ void emit_grad(const RenderParams& p, const TileCtx& 
   }
 }
 
+// Exclusive scan of v over the CTA (NWB warps); total receives the sum. One
+// barrier: every thread adds the totals of the warps before its own. The
+// caller keeps scratch (NWB words) unwritten until a later barrier.
+template <int NWB>
 __device__ __forceinline__ int block_scan_int(int v, int* scratch, int& total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int incl = v;
@@ -1023,23 +1039,15 @@ __device__ __forceinline__ int block_scan_int(int v, int* scratch, int& total) {
   }
   if (lane == 31) scratch[warp] = incl;
   __syncthreads();
-  if (warp == 0) {
-    const int nw = blockDim.x >> 5;
-    const int wv = lane < nw ? scratch[lane] : 0;
-    int wi = wv;
+  int before = 0, all = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int u = __shfl_up_sync(FULL_MASK, wi, o);
-      if (lane >= o) wi += u;
-    }
-    if (lane < nw) scratch[lane] = wi - wv;
-    if (lane == nw - 1) scratch[32] = wi;
+  for (int w = 0; w < NWB; ++w) {
+    const int tw = scratch[w];
+    before += w < warp ? tw : 0;
+    all += tw;
   }
-  __syncthreads();
-  const int r = scratch[warp] + incl - v;
-  total = scratch[32];
-  __syncthreads();
-  return r;
+  total = all;
+  return before + incl - v;
 }
 
 // floor(a / d) for 0 <= a < 2^22 and d >= 1, given inv = 1/d in float32: the
@@ -1065,9 +1073,9 @@ __device__ __forceinline__ int div_small(int a, int d, float inv) {
 // barrier, the thread of candidate j adds A_j and the B_t of the later
 // threads its pairs reach, and turns the sums into parameter gradients.
 // Needs at most NT * 16 pairs (K <= 16): s_win / s_pair hold 16 NT entries.
-template <int TILE, int K, int NC, int CH>
+template <int TILE, int K, int NC, int CH, bool PACK>
 __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx& t, int cnt,
-                                            int nw, const int (&ew)[KS<K>::A],
+                                            int nw, const WinRecs<KS<K>::A, PACK>& ew,
                                             const float4* s_a, const float2* s_b,
                                             const float* s_col, unsigned short* s_win,
                                             unsigned* s_cnt, const float4* s_ps0,
@@ -1088,7 +1096,7 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
     if (tid < cnt) tot += __popc(s_cnt[wb * CH + tid]);
   }
   int P;
-  const int base = block_scan_int(tid < cnt ? tot : 0, s_scan, P);
+  const int base = block_scan_int<NWB>(tid < cnt ? tot : 0, s_scan, P);
   if (tid < cnt) {
 #pragma unroll
     for (int wb = 0; wb < NWB; ++wb) s_cnt[wb * CH + tid] = (unsigned)(base + pre[wb]);
@@ -1098,12 +1106,18 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
   __syncthreads();
   unsigned short* s_pair = s_win;
   const unsigned* s_first = s_cnt + (tid >> 5) * CH;  // first slot of (candidate, my warp block)
+  auto put = [&](int k) {
+    const unsigned rec = ew.get(k);
+    const int j = (int)(rec >> 5);
+    s_pair[s_first[j] + (rec & 31u)] = (unsigned short)((j << 8) | tid);
+  };
+  if (__all_sync(FULL_MASK, nw == A)) {
 #pragma unroll
-  for (int k = 0; k < A; ++k) {
-    if (k < nw) {
-      const int j = ew[k] >> 5;
-      s_pair[s_first[j] + (ew[k] & 31u)] = (unsigned short)((j << 8) | tid);
-    }
+    for (int k = 0; k < A; ++k) put(k);
+  } else {
+#pragma unroll
+    for (int k = 0; k < A; ++k)
+      if (k < nw) put(k);
   }
   const int per = (P + NT - 1) / NT;  // pairs per thread
   const float inv_per = per > 0 ? 1.0f / (float)per : 0.0f;
@@ -1308,7 +1322,8 @@ __device__ __forceinline__ void chunked_pass_c(const RenderParams& p, const Tile
 }
 
 // Adjoint of one tile: passes A and B per pixel, then pass C per candidate.
-template <int TILE, int K, int NC, int CH>
+// PACK: winner records two per register (the persistent batched kernel).
+template <int TILE, int K, int NC, int CH, bool PACK>
 __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t, float* smem) {
   constexpr int NT = TILE * TILE;
   constexpr int NCR = Chan<NC>::R;
@@ -1349,7 +1364,7 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
   const int len = t.range.y - t.range.x;
   const bool fast = len <= CH;
   float tq[KS<K>::A];
-  int ew[KS<K>::A];  // fast path: this pixel's winner records for pass C
+  WinRecs<KS<K>::A, PACK> ew;  // fast path: this pixel's winner records
   PixelBlend<NCR> r;
   __syncthreads();  // the previous tile of a persistent CTA is done with smem
   if (fast) {
@@ -1375,7 +1390,7 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const bool ok = in_img && tk[k] != PK_NONE;
-        ew[k] = ok ? winner_record(tk[k], cnt_w) : 0;
+        ew.set(k, ok ? winner_record(tk[k], cnt_w) : 0);
         r.nw += ok ? 1 : 0;
       }
     } else {
@@ -1389,28 +1404,40 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
     blend_pass<TILE, K, NC, CH>(p, t.range, px, py, tq, r, s_a, s_b, s_col);
   }
 
-  float loss = 0.0f;
+  // per-pixel factors gh_c = -g_c / (2 Z), so that dL/dq_k = w_k (sum_c
+  // gh_c c_k,c - beta) with beta = sum_c gh_c c_r,c; g_c is the upstream
+  // gradient, or sign(c_r,c - c_t,c) / (H W n) for the L1 loss. Pixels
+  // without weight (no winners) get none, but their |c_r - c_t| (c_r = 0)
+  // still counts in the loss.
   const bool live = in_img && r.Z > 0.0f;
+  const float hz = live ? -0.5f * r.iz : 0.0f;
+  const float hl = hz * t.inv_count;
+  float loss = 0.0f;
   float beta = 0.0f;
-  const float iz = live ? r.iz : 0.0f;
+  float gh[NCR];
 #pragma unroll
   for (int c = 0; c < NCR; ++c) {
+    gh[c] = 0.0f;
     if (NC > 0 || c < n) {
-      float g = 0.0f;
-      if (live) {
-        const float u = NC > 0 ? up[NC > 0 ? c : 0] : src[c * plane + o];
-        if (p.grad_img) {
-          g = u;
-        } else {
-          const float d = r.cr[c] - u;
-          loss += fabsf(d);
-          g = sign_f(d) * t.inv_count;
-        }
+      const float u = NC > 0 ? up[NC > 0 ? c : 0] : (in_img ? src[c * plane + o] : 0.0f);
+      if (p.grad_img) {
+        gh[c] = hz * u;
+      } else {
+        const float d = r.cr[c] - u;
+        loss += fabsf(d);
+        gh[c] = d > 0.0f ? hl : (d < 0.0f ? -hl : 0.0f);
       }
-      const float gh = -0.5f * g * iz;  // dL/dq_k = w_k * (sum_c gh_c c_k,c - beta)
-      if (p.normalize) beta = fmaf(gh, r.cr[c], beta);
-      s_gh[gh_at<NC>(threadIdx.x, c, NT)] = gh;
+      if (p.normalize) beta = fmaf(gh[c], r.cr[c], beta);
     }
+  }
+  if (!in_img) loss = 0.0f;
+  if (NC == 3 || NC == 4) {
+    reinterpret_cast<float4*>(s_gh)[threadIdx.x] =
+        make_float4(gh[0], gh[1], gh[2], NC == 4 ? gh[NC == 4 ? 3 : 0] : 0.0f);
+  } else {
+#pragma unroll
+    for (int c = 0; c < NCR; ++c)
+      if (NC > 0 || c < n) s_gh[gh_at<NC>(threadIdx.x, c, NT)] = gh[c];
   }
   s_ps0[threadIdx.x] = make_float4(px, py, r.q0, beta);
   // the chunked pass C (long lists; K = 0, where every candidate wins) re-tests
@@ -1433,7 +1460,7 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
 
   // ---- pass C: candidate-major accumulation of the adjoint
   if (flat) {
-    flat_pass_c<TILE, K, NC, CH>(p, t, len, r.nw, ew, s_a, s_b, s_col, s_win, s_cnt, s_ps0, s_gh,
+    flat_pass_c<TILE, K, NC, CH, PACK>(p, t, len, r.nw, ew, s_a, s_b, s_col, s_win, s_cnt, s_ps0, s_gh,
                                  s_slot_a, s_slot_b, reinterpret_cast<int*>(smem + SL.coff),
                                  reinterpret_cast<int*>(smem + SL.scan));
   } else {
@@ -1445,17 +1472,17 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
 template <int TILE, int K, int NC>
 __global__ void __launch_bounds__(TILE * TILE, TILE == 16 ? 5 : 16) k_render_bwd(RenderParams p) {
   extern __shared__ __align__(16) float smem[];
-  const int tile_id = blockIdx.x;
+  const int tile_id = blockIdx.y * p.tiles_x + blockIdx.x;  // grid (tiles_x, tiles_y)
   TileCtx t;
   t.range = p.range[tile_id];
-  t.x0 = (tile_id % p.tiles_x) * TILE;
-  t.y0 = (tile_id / p.tiles_x) * TILE;
+  t.x0 = blockIdx.x * TILE;
+  t.y0 = blockIdx.y * TILE;
   t.H = p.H;
   t.W = p.W;
   t.off = 0;
   t.inv_count = p.inv_count;
   t.loss_acc = &p.status->loss_sum;
-  bwd_tile<TILE, K, NC, TILE * TILE>(p, t, smem);  // the whole tile's pixels per stage
+  bwd_tile<TILE, K, NC, TILE * TILE, false>(p, t, smem);  // the whole tile's pixels per stage
 }
 
 __device__ __forceinline__ int image_of_tile(const BatchTables& bt, int tile) {
@@ -1473,29 +1500,34 @@ template <int TILE, int K, int NC, int CH>
 __global__ void __launch_bounds__(TILE * TILE, 5) k_render_bwd_batch(RenderParams p,
                                                                   BatchTables bt) {
   extern __shared__ __align__(16) float smem[];
+  // the current tile's context lives in shared memory and is read where it
+  // is used (in registers it would hold about a dozen through the tile)
+  __shared__ TileCtx s_tc;
   __shared__ int s_item;
   int it = blockIdx.x;
   for (;;) {
-    if (bt.order == 0) {
-      if (threadIdx.x == 0) s_item = (int)atomicAdd(bt.work, 1u);
-      __syncthreads();
-      it = s_item;
-      __syncthreads();
+    __syncthreads();  // every thread is done with the previous tile's context
+    if (threadIdx.x == 0) {
+      if (bt.order == 0) it = (int)atomicAdd(bt.work, 1u);
+      s_item = it;
+      if (it < bt.T) {
+        const int b = image_of_tile(bt, it);
+        const int4 dm = bt.dims[b];
+        const int local = it - bt.tile_off[b];
+        s_tc.range = p.range[it];
+        s_tc.x0 = (local % dm.z) * TILE;
+        s_tc.y0 = (local / dm.z) * TILE;
+        s_tc.H = dm.x;
+        s_tc.W = dm.y;
+        s_tc.off = bt.pix_off[b];
+        s_tc.inv_count = 1.0f / ((float)dm.x * (float)dm.y * (float)nchan<NC>(p));
+        s_tc.loss_acc = bt.loss + b;
+      }
     }
+    __syncthreads();
+    it = s_item;
     if (it >= bt.T) break;
-    const int b = image_of_tile(bt, it);
-    const int4 dm = bt.dims[b];
-    const int local = it - bt.tile_off[b];
-    TileCtx t;
-    t.range = p.range[it];
-    t.x0 = (local % dm.z) * TILE;
-    t.y0 = (local / dm.z) * TILE;
-    t.H = dm.x;
-    t.W = dm.y;
-    t.off = bt.pix_off[b];
-    t.inv_count = 1.0f / ((float)dm.x * (float)dm.y * (float)nchan<NC>(p));
-    t.loss_acc = bt.loss + b;
-    bwd_tile<TILE, K, NC, CH>(p, t, smem);
+    bwd_tile<TILE, K, NC, CH, true>(p, s_tc, smem);
     if (bt.order != 0) it += gridDim.x;
   }
 }

@@ -6,13 +6,13 @@ namespace igs {
 namespace {
 
 template <int KK, int NCC>
-cudaError_t fwd_inst(const RenderParams& p, unsigned grid, cudaStream_t s) {
+cudaError_t fwd_inst(const RenderParams& p, dim3 grid, cudaStream_t s) {
   k_render_fwd<16, KK, NCC><<<grid, 16 * 16, 0, s>>>(p);
   return cudaGetLastError();
 }
 
 template <int KK, int NCC>
-cudaError_t bwd_inst(const RenderParams& p, unsigned grid, cudaStream_t s) {
+cudaError_t bwd_inst(const RenderParams& p, dim3 grid, cudaStream_t s) {
   const size_t bytes = sizeof(float) * (size_t)bwd_smem(16 * 16, NCC > 0 ? NCC : p.n, 16 * 16).total;
   if (bytes > 48 * 1024) {
     // the limit is a per-device attribute of the kernel: set on every launch
@@ -37,15 +37,15 @@ cudaError_t bwd_inst(const RenderParams& p, unsigned grid, cudaStream_t s) {
   }
 
 cudaError_t launch_render_fwd_t16(const RenderParams& p, int K, cudaStream_t s) {
-  const unsigned grid = (unsigned)(p.tiles_x * p.tiles_y);
-  if (grid == 0) return cudaSuccess;
+  if (p.tiles_x * p.tiles_y == 0) return cudaSuccess;
+  const dim3 grid((unsigned)p.tiles_x, (unsigned)p.tiles_y);  // one CTA per tile
   IGS_FOR_K(IGS_NC_SWITCH, fwd_inst)
   return cudaSuccess;
 }
 
 cudaError_t launch_render_bwd_t16(const RenderParams& p, int K, cudaStream_t s) {
-  const unsigned grid = (unsigned)(p.tiles_x * p.tiles_y);
-  if (grid == 0) return cudaSuccess;
+  if (p.tiles_x * p.tiles_y == 0) return cudaSuccess;
+  const dim3 grid((unsigned)p.tiles_x, (unsigned)p.tiles_y);  // one CTA per tile
   IGS_FOR_K(IGS_NC_SWITCH, bwd_inst)
   return cudaSuccess;
 }
