@@ -117,6 +117,13 @@ __device__ __forceinline__ float blend_weight(float q0, float q) {
   return y;
 }
 
+// Reciprocal on the MUFU (rcp.approx: within one ulp).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ float sign_f(float x) {
   return x > 0.0f ? 1.0f : (x < 0.0f ? -1.0f : 0.0f);
 }

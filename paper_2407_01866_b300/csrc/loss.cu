@@ -30,10 +30,13 @@ struct Win {
 // One pass per 32 x 32 output tile: the tile's x and y with a 10-pixel halo
 // are staged in shared memory; the window moments and SSIM partials are
 // formed over the tile plus a 5-pixel ring, window-summed again over the
-// tile, and turned into the gradient. Each thread takes 3 or 4 consecutive
-// outputs of a row or column, so that staged values are reused across taps.
+// tile, and turned into the gradient. Each thread takes several consecutive
+// outputs of a row or column (3, VB, HB, 4 in the four passes), so that
+// staged values are reused across taps.
 constexpr int TO = 32;           // output tile edge
 constexpr int TM = TO + 2 * WR;  // 42: window moments and SSIM partials
+constexpr int VB = 7;            // moment rows per thread: 252 tasks, one CTA round
+constexpr int HB = 4;            // partial-sum columns per thread (divides TO)
 constexpr int TI = TO + 4 * WR;  // 52: staged x and y
 constexpr int SSIM_THREADS = 256;
 // shared memory (floats): [x | y] staged (2 TI^2), later the partials G
@@ -54,7 +57,7 @@ struct SsimImages {
   int H, W;
 };
 
-__global__ void __launch_bounds__(SSIM_THREADS) k_ssim_tile(const float* x, const float* y,
+__global__ void __launch_bounds__(SSIM_THREADS, 3) k_ssim_tile(const float* x, const float* y,
                                                             SsimImages im, int n, Win w,
                                                             float w_ssim, float* grad,
                                                             double* acc) {
@@ -82,7 +85,10 @@ __global__ void __launch_bounds__(SSIM_THREADS) k_ssim_tile(const float* x, cons
   const int x0 = (t % tx) * TO, y0 = (t / tx) * TO;
   const int64_t HW = (int64_t)H * W;
   const float inv_m = 1.0f / ((float)n * (float)H * (float)W);
-  double part = 0.0;
+  // this thread's share of the loss: at most a few dozen terms of magnitude
+  // <= max(1, w_ssim) per channel, summed in float32; one float64 atomic per
+  // warp (FP64 arithmetic runs at a small fraction of the FP32 rate)
+  float part = 0.0f;
   for (int c = 0; c < n; ++c) {
     const float* xc = x + off + c * HW;
     const float* yc = y + off + c * HW;
@@ -127,20 +133,21 @@ __global__ void __launch_bounds__(SSIM_THREADS) k_ssim_tile(const float* x, cons
     // vertical sums -> moments -> SSIM and its partials over the TM x TM
     // ring region (zero outside the image); the loss's SSIM term over the
     // tile's own pixels
-    for (int task = tid; task < TM * (TM / 3); task += SSIM_THREADS) {
-      const int jm = task % TM, i0 = (task / TM) * 3;
-      float m[5][3];
+    // (VB rows per task: TM * TM / VB = 252 tasks, one round of the CTA)
+    for (int task = tid; task < TM * (TM / VB); task += SSIM_THREADS) {
+      const int jm = task % TM, i0 = (task / TM) * VB;
+      float m[5][VB];
 #pragma unroll
       for (int k = 0; k < 5; ++k)
 #pragma unroll
-        for (int o = 0; o < 3; ++o) m[k][o] = 0.0f;
+        for (int o = 0; o < VB; ++o) m[k][o] = 0.0f;
 #pragma unroll
-      for (int e = 0; e < 2 * WR + 3; ++e) {
+      for (int e = 0; e < 2 * WR + VB; ++e) {
         float v[5];
 #pragma unroll
         for (int k = 0; k < 5; ++k) v[k] = sB[(k * TI + i0 + e) * TM + jm];
 #pragma unroll
-        for (int o = 0; o < 3; ++o) {
+        for (int o = 0; o < VB; ++o) {
           const int i = e - o;
           if (i < 0 || i > 2 * WR) continue;
 #pragma unroll
@@ -148,7 +155,7 @@ __global__ void __launch_bounds__(SSIM_THREADS) k_ssim_tile(const float* x, cons
         }
       }
 #pragma unroll
-      for (int o = 0; o < 3; ++o) {
+      for (int o = 0; o < VB; ++o) {
         const int ii = i0 + o;
         const int py = y0 - WR + ii, px = x0 - WR + jm;
         float g1 = 0.0f, g2 = 0.0f, g3 = 0.0f;
@@ -157,7 +164,7 @@ __global__ void __launch_bounds__(SSIM_THREADS) k_ssim_tile(const float* x, cons
           const float vx = m[2][o] - mx * mx, vy = m[3][o] - my * my, cxy = m[4][o] - mx * my;
           const float A1 = 2.f * mx * my + C1, A2 = 2.f * cxy + C2;
           const float B1 = mx * mx + my * my + C1, B2 = vx + vy + C2;
-          const float iB = 1.f / (B1 * B2);
+          const float iB = rcp_approx(B1 * B2);
           const float S = A1 * A2 * iB;
           const float dS_dvx = -S * (B1 * iB);   // -S / B2
           const float dS_dcxy = 2.f * A1 * iB;
@@ -166,7 +173,7 @@ __global__ void __launch_bounds__(SSIM_THREADS) k_ssim_tile(const float* x, cons
           g2 = dS_dvx;
           g3 = dS_dcxy;
           if (ii >= WR && ii < WR + TO && jm >= WR && jm < WR + TO)
-            part += (double)w_ssim * (1.0 - (double)S);
+            part += w_ssim * (1.0f - S);
         }
         sA[(0 * TM + ii) * TM + jm] = g1;
         sA[(1 * TM + ii) * TM + jm] = g2;
@@ -175,20 +182,21 @@ __global__ void __launch_bounds__(SSIM_THREADS) k_ssim_tile(const float* x, cons
     }
     __syncthreads();
     // horizontal window sums of the partials: rows TM, columns TO
-    for (int task = tid; task < TM * (TO / 4); task += SSIM_THREADS) {
-      const int r = task / (TO / 4), j0 = (task % (TO / 4)) * 4;
-      float s[3][4];
+    // (HB columns per task; 8 was no faster)
+    for (int task = tid; task < TM * (TO / HB); task += SSIM_THREADS) {
+      const int r = task / (TO / HB), j0 = (task % (TO / HB)) * HB;
+      float s[3][HB];
 #pragma unroll
       for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int o = 0; o < 4; ++o) s[k][o] = 0.0f;
+        for (int o = 0; o < HB; ++o) s[k][o] = 0.0f;
 #pragma unroll
-      for (int e = 0; e < 2 * WR + 4; ++e) {
+      for (int e = 0; e < 2 * WR + HB; ++e) {
         float v[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) v[k] = sA[(k * TM + r) * TM + j0 + e];
 #pragma unroll
-        for (int o = 0; o < 4; ++o) {
+        for (int o = 0; o < HB; ++o) {
           const int i = e - o;
           if (i < 0 || i > 2 * WR) continue;
 #pragma unroll
@@ -198,7 +206,7 @@ __global__ void __launch_bounds__(SSIM_THREADS) k_ssim_tile(const float* x, cons
 #pragma unroll
       for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int o = 0; o < 4; ++o) sB[(k * TM + r) * TO + j0 + o] = s[k][o];
+        for (int o = 0; o < HB; ++o) sB[(k * TM + r) * TO + j0 + o] = s[k][o];
     }
     __syncthreads();
     // vertical sums -> dL/dx over the tile: sign(x - y)/M - (w/M)(bG1 + 2x bG2 + y bG3)
@@ -232,12 +240,12 @@ __global__ void __launch_bounds__(SSIM_THREADS) k_ssim_tile(const float* x, cons
         const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
         grad[off + c * HW + p] =
             sgn * inv_m - w_ssim * inv_m * (s[0][o] + 2.f * xv * s[1][o] + yv * s[2][o]);
-        part += (double)fabsf(d);
+        part += fabsf(d);
       }
     }
   }
-  part = warp_sum<double>(part);
-  if ((tid & 31) == 0 && part != 0.0) atomicAdd(acc + b, part);
+  part = warp_sum<float>(part);
+  if ((tid & 31) == 0 && part != 0.0f) atomicAdd(acc + b, (double)part);
 }
 
 // L1 only: gradient and loss sum.

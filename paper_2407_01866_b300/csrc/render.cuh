@@ -83,13 +83,6 @@ __device__ __forceinline__ float4 block_rect(int x0, int y0) {
 constexpr float F_INF = __builtin_huge_valf();
 constexpr int GID_NONE = 0x7fffffff;  // tie cut-off that admits every index
 
-// Reciprocal on the MUFU (rcp.approx: within one ulp).
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 
 // Staged candidate record in shared memory:
 //   a = (mx, my, A00, B)   geometry of the ranking key
