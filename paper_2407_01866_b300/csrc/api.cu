@@ -68,6 +68,7 @@ WsLayout ws_layout_tiles(int64_t N, int n, int64_t T, int64_t m_cap) {
   L.tmp = take(sizeof(unsigned int) * (size_t)m_cap);
   L.big = take(sizeof(int) * (size_t)T);
   L.wide = take(sizeof(int) * (size_t)N);
+  L.wide_geo = take(sizeof(float4) * (size_t)N);
   L.range = take(sizeof(int2) * (size_t)T);
   L.total = o;
   return L;
@@ -280,6 +281,7 @@ int igs_preprocess_bin(const igs_gaussians* g, int32_t H, int32_t W, const igs_c
   p.tmp = reinterpret_cast<unsigned int*>(base + L.tmp);
   p.big = reinterpret_cast<int*>(base + L.big);
   p.wide = reinterpret_cast<int*>(base + L.wide);
+  p.wide_geo = reinterpret_cast<float4*>(base + L.wide_geo);
   p.m_cap = m_capacity;
   p.status = status;
   unsigned long long* part = reinterpret_cast<unsigned long long*>(base + L.part);

@@ -169,6 +169,7 @@ int batch_bin(const float* params, const BatchGeom& G, const igs_config* cfg, ch
   p.tmp = reinterpret_cast<unsigned int*>(base + L.tmp);
   p.big = reinterpret_cast<int*>(base + L.big);
   p.wide = reinterpret_cast<int*>(base + L.wide);
+  p.wide_geo = reinterpret_cast<float4*>(base + L.wide_geo);
   p.m_cap = m_cap;
   p.status = status;
   p.img_of = reinterpret_cast<const int*>(base + G.img_of);

@@ -92,7 +92,9 @@ __global__ void __launch_bounds__(256) k_preprocess(PrepParams p) {
     tile_span(my, r, p.tile, ig.tiles_y, y0, y1);
     const float r2 = __fmul_rn(r, r);
     if ((x1 - x0 + 1) * (y1 - y0 + 1) > WIDE_TILES) {
-      p.wide[atomicAdd(&p.status->wide_cnt, 1u)] = (int)i;
+      const unsigned slot = atomicAdd(&p.status->wide_cnt, 1u);
+      p.wide[slot] = (int)i;
+      p.wide_geo[slot] = make_float4(mx, my, r, __int_as_float((int)i));
       y1 = y0 - 1;  // counted by k_count_wide
     }
     for (int ty = y0; ty <= y1; ++ty) {
@@ -156,14 +158,15 @@ __global__ void __launch_bounds__(256) k_emit(PrepParams p) {
   }
 }
 
-// Wide Gaussians, one CTA each: threads stride over the tile box and apply
-// the same circle-rectangle test. COUNT: increment the tile counters;
-// otherwise: take the tiles' slots (after the scan).
+// Wide Gaussians, one CTA each (CTA cta of ncta): threads stride over the
+// tile box and apply the same circle-rectangle test. COUNT: increment the
+// tiles' counters; otherwise: take the tiles' slots (after the scan).
 template <bool BATCH, bool COUNT>
-__global__ void __launch_bounds__(256) k_wide(PrepParams p) {
+__device__ __forceinline__ void wide_by_gaussian(const PrepParams& p, unsigned cta,
+                                                 unsigned ncta) {
   const unsigned int nw = p.status->wide_cnt;
   const unsigned long long cap = (unsigned long long)p.m_cap;
-  for (unsigned int wi = blockIdx.x; wi < nw; wi += gridDim.x) {
+  for (unsigned int wi = cta; wi < nw; wi += ncta) {
     const int i = p.wide[wi];
     const ImgGeo ig = image_geo<BATCH>(p, i);
     const GRec g = p.rec[i];
@@ -187,6 +190,90 @@ __global__ void __launch_bounds__(256) k_wide(PrepParams p) {
         if (pos < cap) p.vals[pos] = (unsigned int)i;
       }
     }
+  }
+}
+
+template <bool BATCH, bool COUNT>
+__global__ void __launch_bounds__(256) k_wide(PrepParams p) {
+  wide_by_gaussian<BATCH, COUNT>(p, blockIdx.x, gridDim.x);
+}
+
+constexpr int WT_BLOCK = 8;              // tiles per side of k_wide_tiles' tile block
+constexpr int WT_CHUNK = 256;            // wide Gaussians filtered per round
+constexpr unsigned WT_MAX_WIDE = 1u << 14;  // beyond this, one CTA per wide Gaussian
+
+// Wide Gaussians of one image, tile-major: each CTA owns a block of 8 x 8
+// tiles, keeps the wide Gaussians whose circle meets the block's rectangle
+// (a circle that meets a tile meets the block that holds it) and tests them
+// against each of its tiles with the same circle-rectangle test, 4 threads
+// per tile. No tile counter is shared with another CTA. COUNT adds each
+// tile's hits to its counter (after k_preprocess's narrow hits); otherwise
+// the hits take the first slots of the tile's segment from on-chip counters
+// (k_emit fills the segment down from its top, so the two never meet). With
+// more than WT_MAX_WIDE wide Gaussians, where testing every block against
+// every Gaussian would cost more than their hits, the CTAs take one Gaussian
+// each (k_wide's scheme).
+template <bool COUNT>
+__global__ void __launch_bounds__(256) k_wide_tiles(PrepParams p) {
+  const unsigned nw = p.status->wide_cnt;
+  if (nw == 0) return;
+  if (nw > WT_MAX_WIDE) {
+    wide_by_gaussian<false, COUNT>(p, blockIdx.x, gridDim.x);
+    return;
+  }
+  const int bxs = (p.tiles_x + WT_BLOCK - 1) / WT_BLOCK;
+  const int bys = (p.tiles_y + WT_BLOCK - 1) / WT_BLOCK;
+  if ((int)blockIdx.x >= bxs * bys) return;  // the grid also serves the other scheme
+  const int bx = (int)blockIdx.x % bxs, by = (int)blockIdx.x / bxs;
+  __shared__ float4 s_g[WT_CHUNK];  // (mx, my, r^2, index bits) meeting the block
+  __shared__ int s_n;
+  __shared__ int s_slot[WT_BLOCK * WT_BLOCK];
+  const int tid = threadIdx.x;
+  const int tl = tid >> 2, q = tid & 3;  // tile of the block, thread within the tile
+  const int tx = bx * WT_BLOCK + (tl % WT_BLOCK);
+  const int ty = by * WT_BLOCK + (tl / WT_BLOCK);
+  const bool tile_ok = tx < p.tiles_x && ty < p.tiles_y;
+  const float X0 = (float)(tx * p.tile), X1 = (float)min((tx + 1) * p.tile, p.W);
+  const float Y0 = (float)(ty * p.tile), Y1 = (float)min((ty + 1) * p.tile, p.H);
+  const int bx0 = bx * WT_BLOCK * p.tile, by0 = by * WT_BLOCK * p.tile;
+  const float BX0 = (float)bx0, BX1 = (float)min(bx0 + WT_BLOCK * p.tile, p.W);
+  const float BY0 = (float)by0, BY1 = (float)min(by0 + WT_BLOCK * p.tile, p.H);
+  const int t = ty * p.tiles_x + tx;
+  const unsigned long long cap = (unsigned long long)p.m_cap;
+  const unsigned long long seg = COUNT || !tile_ok ? 0ull : p.toff[t];
+  if (tid < WT_BLOCK * WT_BLOCK) s_slot[tid] = 0;
+  int hits = 0;
+  float4 nxt = (unsigned)tid < nw ? p.wide_geo[tid] : make_float4(0.f, 0.f, -1.f, 0.f);
+  for (unsigned base = 0; base < nw; base += WT_CHUNK) {
+    __syncthreads();  // the previous round is done with s_g
+    if (tid == 0) s_n = 0;
+    __syncthreads();
+    const float4 g = nxt;  // (mx, my, r, index bits) of wide Gaussian base + tid
+    if (base + tid < nw) {
+      const float r2 = __fmul_rn(g.z, g.z);
+      if (circle_hits_rect(g.x, g.y, r2, BX0, BX1, BY0, BY1))
+        s_g[atomicAdd(&s_n, 1)] = make_float4(g.x, g.y, r2, g.w);
+    }
+    // the next round's record, in flight during this round's tests
+    if (base + WT_CHUNK + tid < nw) nxt = p.wide_geo[base + WT_CHUNK + tid];
+    __syncthreads();
+    const int n = s_n;
+    if (!tile_ok) continue;
+    for (int k = q; k < n; k += 4) {
+      const float4 c = s_g[k];
+      if (!circle_hits_rect(c.x, c.y, c.z, X0, X1, Y0, Y1)) continue;
+      if (COUNT) {
+        ++hits;
+      } else {
+        const unsigned long long pos = seg + (unsigned)atomicAdd(&s_slot[tl], 1);
+        if (pos < cap) p.vals[pos] = (unsigned int)__float_as_int(c.w);
+      }
+    }
+  }
+  if (COUNT) {
+    hits += __shfl_down_sync(FULL_MASK, hits, 2, 4);
+    hits += __shfl_down_sync(FULL_MASK, hits, 1, 4);
+    if (q == 0 && tile_ok && hits) p.tcnt[t] += (unsigned)hits;
   }
 }
 
@@ -641,10 +728,13 @@ cudaError_t run_binning(const PrepParams& p, int dtype, int T, unsigned long lon
   if (e != cudaSuccess) return e;
   if ((e = launch_preprocess(p, dtype, s)) != cudaSuccess) return e;
   const bool batch = p.img_of != nullptr;
-  // one CTA per wide Gaussian (up to WIDE_GRID at a time): their hits take
-  // returning atomics, so many boxes must be in flight at once
+  // one image: tile blocks own their tiles' wide hits; a batch: one CTA per
+  // wide Gaussian (up to WIDE_GRID at a time)
+  const int64_t wt_blocks = (int64_t)((p.tiles_x + WT_BLOCK - 1) / WT_BLOCK) *
+                            ((p.tiles_y + WT_BLOCK - 1) / WT_BLOCK);
+  const unsigned wt_grid = (unsigned)std::max<int64_t>(wt_blocks, WIDE_GRID);
   if (batch) k_wide<true, true><<<WIDE_GRID, 256, 0, s>>>(p);
-  else k_wide<false, true><<<WIDE_GRID, 256, 0, s>>>(p);
+  else if (T > 0) k_wide_tiles<true><<<wt_grid, 256, 0, s>>>(p);
   // the tile scan; for one image its last pass also writes the tile ranges
   // and the evaluation count (the batch gets them from k_ranges and its own
   // evaluation kernel after the emission)
@@ -663,7 +753,7 @@ cudaError_t run_binning(const PrepParams& p, int dtype, int T, unsigned long lon
   }
   if ((e = launch_emit(p, s)) != cudaSuccess) return e;
   if (batch) k_wide<true, false><<<WIDE_GRID, 256, 0, s>>>(p);
-  else k_wide<false, false><<<WIDE_GRID, 256, 0, s>>>(p);
+  else if (T > 0) k_wide_tiles<false><<<wt_grid, 256, 0, s>>>(p);
   if ((e = launch_segsort(p.vals, p.tmp, p.toff, T, p.status, p.m_cap, p.big, sort_min, s)) !=
       cudaSuccess)
     return e;

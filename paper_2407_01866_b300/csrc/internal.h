@@ -16,7 +16,8 @@ constexpr int SCAN_ITEMS = SCAN_THREADS * SCAN_PER_THREAD;
 
 // Byte offsets of the workspace sections (all 256-byte aligned).
 struct WsLayout {
-  size_t status, rec, trig, color, rec16, col16, tcnt, toff, part, vals, tmp, big, wide, range;
+  size_t status, rec, trig, color, rec16, col16, tcnt, toff, part, vals, tmp, big, wide, wide_geo,
+      range;
   size_t total;
   int64_t part_len;     // scan partials entries
   int tiles_x, tiles_y;
@@ -48,6 +49,7 @@ struct PrepParams {
   unsigned int* tmp;            // [m_cap] merge buffer of long segments
   int* big;                     // [T] tiles whose segment is sorted by a CTA
   int* wide;                    // [N] Gaussians whose tile box is binned by a CTA
+  float4* wide_geo;             // [N] their (mx, my, r, index bits), same order
   int64_t m_cap;
   DevStatus* status;
   // batched form: image of each Gaussian, per-image (H, W, tiles_x, tiles_y)

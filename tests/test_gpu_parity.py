@@ -61,6 +61,30 @@ def test_tile_lists_equal_oracle_sets(case):
     assert gs.stats.flags == 0
 
 
+# Gaussians whose tile box exceeds 64 tiles are binned by a separate pass:
+# tile blocks testing every such Gaussian (several rounds of 256 here), and
+# beyond 16384 of them one CTA per Gaussian
+WIDE_CASES = [
+    (512, 512, 3000, 1, 16, 21, (10.0, 20.0)),
+    (384, 320, 20000, 1, 16, 22, (20.0, 40.0)),
+]
+
+
+@pytest.mark.parametrize("case", WIDE_CASES, ids=lambda c: f"{c[0]}x{c[1]}_N{c[2]}")
+def test_tile_lists_with_many_wide_gaussians(case):
+    H, W, N, n, tile, seed, sr = case
+    g = oset(N, n, seed, sr)
+    want = O.tile_lists(g, H, W, tile)
+    M = sum(len(w) for w in want)
+    gs = GpuSet(g, H, W, 4, tile, m_capacity=M + 1024)
+    got = gs.tile_lists()
+    for j, (a, b) in enumerate(zip(got, want)):
+        np.testing.assert_array_equal(a if len(a) > tile * tile else np.sort(a), b,
+                                      err_msg=f"tile {j}")
+    assert gs.stats.m_needed == M
+    assert gs.stats.flags == 0
+
+
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}_N{c[2]}_n{c[3]}_K{c[4]}_t{c[5]}")
 def test_forward_matches_oracle(case):
     H, W, N, n, K, tile, seed, sr = case
