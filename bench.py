@@ -410,7 +410,11 @@ def run_ours(args, w=WORKLOAD):
     # Every step copies its target from pinned host memory and reads its loss
     # back. Two device target buffers, each with its own captured step: the
     # copy for step k+1 (on a copy stream) overlaps step k.
-    tgt_host = torch.from_numpy(target_np).pin_memory()
+    # the pinned copy is filled through its numpy view: host-to-device copies
+    # from pinned pages written that way measured 55 GB/s, against 17-27 GB/s
+    # after torch's own CPU copy or fill into the same pages
+    tgt_host = torch.empty(target_np.shape, dtype=torch.float32, pin_memory=True)
+    tgt_host.numpy()[...] = target_np
     loss_host = torch.zeros(1).pin_memory()
     e_steps = max(3, min(args.steps, 50))
     targets = [target, torch.empty_like(target)]
@@ -420,6 +424,9 @@ def run_ours(args, w=WORKLOAD):
         target = targets[1]
         step_fn()
     target = target_now
+    # the second graph's first replay uploads it: once, untimed, on a real target
+    targets[1].copy_(target)
+    graphs[1].replay()
     cs = torch.cuda.Stream(device=dev)
     comp = torch.cuda.current_stream()
     copied = [torch.cuda.Event(), torch.cuda.Event()]
