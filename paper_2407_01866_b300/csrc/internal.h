@@ -11,7 +11,7 @@ namespace igs {
 
 // Scan geometry: one block scans SCAN_THREADS * SCAN_PER_THREAD entries.
 constexpr int SCAN_THREADS = 512;
-constexpr int SCAN_PER_THREAD = 8;
+constexpr int SCAN_PER_THREAD = 2;
 constexpr int SCAN_ITEMS = SCAN_THREADS * SCAN_PER_THREAD;
 
 // Byte offsets of the workspace sections (all 256-byte aligned).
