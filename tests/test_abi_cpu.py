@@ -82,6 +82,13 @@ def test_workspace_size_grows_with_inputs_and_validates(lib):
         L.workspace_size(1000, 0, 256, 256, c, 10_000)
     with pytest.raises(L.IgsError):
         L.workspace_size(1000, 3, 0, 256, c, 10_000)
+    # the render grid has one CTA per tile and at most 65535 rows of tiles
+    c8 = L.default_config(tile=8)
+    assert L.workspace_size(1000, 3, 8 * 65535, 16, c8, 10_000) > 0
+    with pytest.raises(L.IgsError) as e:
+        L.workspace_size(1000, 3, 8 * 65535 + 1, 16, c8, 10_000)
+    assert e.value.code == L.IGS_ERR_INVALID_ARG
+    assert "65535" in str(e.value)
 
 
 def test_entry_points_reject_bad_arguments_without_a_gpu(lib):
