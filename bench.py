@@ -47,9 +47,9 @@ FUSED_TRAFFIC_2048_RGB = 62_361_344
 TRAFFIC_STEPS_MAX = 50
 # library kernels of one fit step (the ncu launch list of the bench): finalize,
 # preprocess, 2 wide-Gaussian passes, 3 scan passes (the last also writes the
-# tile ranges and the evaluation count), emit, 2 segment sorts, fused adjoint,
-# Adam
-KERNELS_PER_FIT_STEP = 12
+# tile ranges and the evaluation count), emit, the sort of long lists, fused
+# adjoint, Adam
+KERNELS_PER_FIT_STEP = 11
 # the SSIM term adds the forward render and the one-pass image loss
 SSIM_EXTRA_KERNELS = 2
 

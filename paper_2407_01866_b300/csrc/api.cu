@@ -66,7 +66,6 @@ WsLayout ws_layout_tiles(int64_t N, int n, int64_t T, int64_t m_cap) {
   L.part = take(sizeof(unsigned long long) * (size_t)L.part_len);
   L.vals = take(sizeof(unsigned int) * (size_t)m_cap);
   L.tmp = take(sizeof(unsigned int) * (size_t)m_cap);
-  L.big = take(sizeof(int) * (size_t)T);
   L.wide = take(sizeof(int) * (size_t)N);
   L.wide_geo = take(sizeof(float4) * (size_t)N);
   L.range = take(sizeof(int2) * (size_t)T);
@@ -279,7 +278,6 @@ int igs_preprocess_bin(const igs_gaussians* g, int32_t H, int32_t W, const igs_c
   p.toff = reinterpret_cast<unsigned long long*>(base + L.toff);
   p.vals = reinterpret_cast<unsigned int*>(base + L.vals);
   p.tmp = reinterpret_cast<unsigned int*>(base + L.tmp);
-  p.big = reinterpret_cast<int*>(base + L.big);
   p.wide = reinterpret_cast<int*>(base + L.wide);
   p.wide_geo = reinterpret_cast<float4*>(base + L.wide_geo);
   p.m_cap = m_capacity;

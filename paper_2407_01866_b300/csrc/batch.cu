@@ -167,7 +167,6 @@ int batch_bin(const float* params, const BatchGeom& G, const igs_config* cfg, ch
   p.toff = reinterpret_cast<unsigned long long*>(base + L.toff);
   p.vals = reinterpret_cast<unsigned int*>(base + L.vals);
   p.tmp = reinterpret_cast<unsigned int*>(base + L.tmp);
-  p.big = reinterpret_cast<int*>(base + L.big);
   p.wide = reinterpret_cast<int*>(base + L.wide);
   p.wide_geo = reinterpret_cast<float4*>(base + L.wide_geo);
   p.m_cap = m_cap;

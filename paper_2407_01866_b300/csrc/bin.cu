@@ -9,13 +9,14 @@
 //                  (for one image its last pass also writes the tile ranges
 //                  and the evaluation count)
 //   k_emit         every hit takes a slot of its tile's segment (atomic cursor)
-//   k_segsort      a warp sorts a tile's segment by Gaussian index when it
-//                  is longer than the renderer's one-stage list
-//                  (longer lists are streamed in index order, which is the
-//                  tie-break order of the top-K ranking; shorter ones are
-//                  ranked by the renderer itself); segments longer than one
-//                  warp's shared-memory window are sorted by whole CTAs in
-//                  k_segsort_big
+//   k_wide_tiles   Gaussians whose tile box exceeds 64 tiles (one image):
+//                  counted and emitted tile-major by 8 x 8 tile blocks
+//                  (k_wide, one CTA per such Gaussian, for a batch)
+//   k_segsort_long a CTA sorts each tile's segment by Gaussian index when it
+//                  is longer than the renderer's one-stage list (longer lists
+//                  are streamed in index order, which is the tie-break order
+//                  of the top-K ranking; shorter ones are ranked by the
+//                  renderer itself)
 //   k_ranges       [start, end) of every tile from the offsets, and the sum
 //                  over tiles of |S_j| * pixels(j)
 #include <algorithm>
@@ -439,166 +440,117 @@ __device__ __forceinline__ void tile_segment(const unsigned long long* toff, int
   b = b < M ? b : M;
 }
 
-constexpr int SEG_WARP_MAX = 64;    // longest segment one warp sorts (latency-bound beyond)
 constexpr int SEG_BIG_CHUNK = 4096; // run length a CTA sorts in shared memory
 
-// Ascending sort of one tile segment [a, a+L) by the calling warp
-// (1 < L <= SEG_WARP_MAX); w is the warp's shared-memory window.
-__device__ __forceinline__ void warp_sort_segment(unsigned int* vals, int64_t a, int L,
-                                                  unsigned int* w) {
-  const int lane = threadIdx.x & 31;
-  if (L <= 32) {  // bitonic network across the lanes
-    unsigned int v = lane < L ? vals[a + lane] : 0xffffffffu;
-#pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
+// Ascending sort of tile t's segment by the calling CTA: runs of up to
+// SEG_BIG_CHUNK sorted in shared memory (a rank sort up to 512 entries, a
+// bitonic network over the run rounded up to a power of two beyond), then
+// pairwise merges between vals and tmp, each element placed by its rank (its
+// index in its own run plus a binary search in the other run; indices are
+// distinct, so the ranks are a permutation).
+__device__ void sort_segment_cta(unsigned int* vals, unsigned int* tmp,
+                                 const unsigned long long* toff, int t, int T,
+                                 const DevStatus* st, int64_t m_cap, unsigned int* sh) {
+  int64_t a, b;
+  tile_segment(toff, t, T, st, m_cap, a, b);
+  const int L = (int)(b - a);
+  for (int c0 = 0; c0 < L; c0 += SEG_BIG_CHUNK) {
+    const int n = min(SEG_BIG_CHUNK, L - c0);
+    if (n <= 2 * 256) {
+      // rank sort, two entries per thread: an entry's place is the number
+      // of smaller entries (equal ones, only in a corrupt list, by position)
+      __syncthreads();
+      const int i0 = threadIdx.x, i1 = threadIdx.x + 256;
+      const unsigned int v0 = i0 < n ? vals[a + c0 + i0] : 0u;
+      const unsigned int v1 = i1 < n ? vals[a + c0 + i1] : 0u;
+      if (i0 < n) sh[i0] = v0;
+      if (i1 < n) sh[i1] = v1;
+      __syncthreads();
+      int r0 = 0, r1 = 0;
+      for (int j = 0; j < n; ++j) {
+        const unsigned int x = sh[j];
+        r0 += (x < v0 || (x == v0 && j < i0)) ? 1 : 0;
+        r1 += (x < v1 || (x == v1 && j < i1)) ? 1 : 0;
+      }
+      if (i0 < n) vals[a + c0 + r0] = v0;
+      if (i1 < n) vals[a + c0 + r1] = v1;
+      continue;
+    }
+    int P = 64;  // bitonic width: the chunk rounded up to a power of two
+    while (P < n) P <<= 1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < P; i += blockDim.x)
+      sh[i] = i < n ? vals[a + c0 + i] : 0xffffffffu;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
       for (int j = k >> 1; j > 0; j >>= 1) {
-        const unsigned int u = __shfl_xor_sync(FULL_MASK, v, j);
-        const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
-        v = keep_min ? min(v, u) : max(v, u);
-      }
-    }
-    if (lane < L) vals[a + lane] = v;
-    return;
-  }
-  int P = 64;
-  while (P < L) P <<= 1;
-  for (int i = lane; i < P; i += 32) w[i] = i < L ? vals[a + i] : 0xffffffffu;
-  __syncwarp();
-  for (int k = 2; k <= P; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = lane; i < P; i += 32) {
-        const int l = i ^ j;
-        if (l > i) {
-          const unsigned int x = w[i], y = w[l];
-          if ((x > y) == ((i & k) == 0)) {
-            w[i] = y;
-            w[l] = x;
-          }
-        }
-      }
-      __syncwarp();
-    }
-  }
-  for (int i = lane; i < L; i += 32) vals[a + i] = w[i];
-  __syncwarp();
-}
-
-// Ascending sort of the tile segments longer than sort_min. Each warp looks
-// at 32 tiles at a time (one coalesced read of their offsets) and sorts the
-// short ones that need it; longer segments are listed for k_segsort_big.
-__global__ void __launch_bounds__(256) k_segsort(unsigned int* vals,
-                                                 const unsigned long long* toff, int T,
-                                                 DevStatus* st, int64_t m_cap, int* big,
-                                                 int sort_min) {
-  __shared__ unsigned int sh[8][SEG_WARP_MAX];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * 8;
-  for (int base = (blockIdx.x * 8 + warp) * 32; base < T; base += nwarps * 32) {
-    const int t = base + lane;
-    int64_t a = 0, b = 0;
-    if (t < T) tile_segment(toff, t, T, st, m_cap, a, b);
-    const int L = (int)(b - a);
-    const bool longer = t < T && L > 1 && L > sort_min;
-    if (longer && L > SEG_WARP_MAX) big[atomicAdd(&st->big_cnt, 1u)] = t;
-    unsigned need = __ballot_sync(FULL_MASK, longer && L <= SEG_WARP_MAX);
-    while (need) {
-      const int l = __ffs(need) - 1;
-      need &= need - 1;
-      const long long al = __shfl_sync(FULL_MASK, (long long)a, l);
-      const int Ll = __shfl_sync(FULL_MASK, L, l);
-      warp_sort_segment(vals, al, Ll, sh[warp]);
-    }
-  }
-}
-
-// Long segments, one CTA each: runs of up to SEG_BIG_CHUNK sorted in shared
-// memory (bitonic over the run rounded up to a power of two),
-// then pairwise merges between vals and tmp, each element placed by its rank
-// (its index in its own run plus a binary search in the other run; indices
-// are distinct, so the ranks are a permutation).
-__global__ void __launch_bounds__(256) k_segsort_big(unsigned int* vals, unsigned int* tmp,
-                                                      const unsigned long long* toff, int T,
-                                                      const DevStatus* st, int64_t m_cap,
-                                                      const int* big) {
-  __shared__ unsigned int sh[SEG_BIG_CHUNK];
-  const unsigned int nbig = st->big_cnt;
-  for (unsigned int bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
-    const int t = big[bi];
-    int64_t a, b;
-    tile_segment(toff, t, T, st, m_cap, a, b);
-    const int L = (int)(b - a);
-    for (int c0 = 0; c0 < L; c0 += SEG_BIG_CHUNK) {
-      const int n = min(SEG_BIG_CHUNK, L - c0);
-      if (n <= 2 * 256) {
-        // rank sort, two entries per thread: an entry's place is the number
-        // of smaller entries (equal ones, only in a corrupt list, by position)
-        __syncthreads();
-        const int i0 = threadIdx.x, i1 = threadIdx.x + 256;
-        const unsigned int v0 = i0 < n ? vals[a + c0 + i0] : 0u;
-        const unsigned int v1 = i1 < n ? vals[a + c0 + i1] : 0u;
-        if (i0 < n) sh[i0] = v0;
-        if (i1 < n) sh[i1] = v1;
-        __syncthreads();
-        int r0 = 0, r1 = 0;
-        for (int j = 0; j < n; ++j) {
-          const unsigned int x = sh[j];
-          r0 += (x < v0 || (x == v0 && j < i0)) ? 1 : 0;
-          r1 += (x < v1 || (x == v1 && j < i1)) ? 1 : 0;
-        }
-        if (i0 < n) vals[a + c0 + r0] = v0;
-        if (i1 < n) vals[a + c0 + r1] = v1;
-        continue;
-      }
-      int P = 64;  // bitonic width: the chunk rounded up to a power of two
-      while (P < n) P <<= 1;
-      __syncthreads();
-      for (int i = threadIdx.x; i < P; i += blockDim.x)
-        sh[i] = i < n ? vals[a + c0 + i] : 0xffffffffu;
-      __syncthreads();
-      for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-          for (int i = threadIdx.x; i < P; i += blockDim.x) {
-            const int l = i ^ j;
-            if (l > i) {
-              const unsigned int x = sh[i], y = sh[l];
-              if ((x > y) == ((i & k) == 0)) {
-                sh[i] = y;
-                sh[l] = x;
-              }
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+          const int l = i ^ j;
+          if (l > i) {
+            const unsigned int x = sh[i], y = sh[l];
+            if ((x > y) == ((i & k) == 0)) {
+              sh[i] = y;
+              sh[l] = x;
             }
           }
-          __syncthreads();
         }
+        __syncthreads();
       }
-      for (int i = threadIdx.x; i < n; i += blockDim.x) vals[a + c0 + i] = sh[i];
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) vals[a + c0 + i] = sh[i];
+  }
+  __syncthreads();
+  unsigned int* src = vals + a;
+  unsigned int* dst = tmp + a;
+  for (int run = SEG_BIG_CHUNK; run < L; run <<= 1) {
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+      const int r0 = (i / (2 * run)) * (2 * run);
+      const bool first = i - r0 < run;
+      const int o0 = first ? r0 + run : r0;          // the other run
+      const int o1 = first ? min(r0 + 2 * run, L) : r0 + run;
+      const unsigned int v = src[i];
+      int lo = o0, hi = o1;                          // elements of the other run below v
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (src[mid] < v) lo = mid + 1; else hi = mid;
+      }
+      const int own = first ? i - r0 : i - (r0 + run);
+      dst[r0 + own + (lo - o0)] = v;
     }
     __syncthreads();
-    unsigned int* src = vals + a;
-    unsigned int* dst = tmp + a;
-    for (int run = SEG_BIG_CHUNK; run < L; run <<= 1) {
-      for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        const int r0 = (i / (2 * run)) * (2 * run);
-        const bool first = i - r0 < run;
-        const int o0 = first ? r0 + run : r0;          // the other run
-        const int o1 = first ? min(r0 + 2 * run, L) : r0 + run;
-        const unsigned int v = src[i];
-        int lo = o0, hi = o1;                          // elements of the other run below v
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (src[mid] < v) lo = mid + 1; else hi = mid;
-        }
-        const int own = first ? i - r0 : i - (r0 + run);
-        dst[r0 + own + (lo - o0)] = v;
-      }
-      __syncthreads();
-      unsigned int* x = src;
-      src = dst;
-      dst = x;
+    unsigned int* x = src;
+    src = dst;
+    dst = x;
+  }
+  if (src != vals + a)
+    for (int i = threadIdx.x; i < L; i += blockDim.x) vals[a + i] = src[i];
+  __syncthreads();
+}
+
+// Every tile segment longer than sort_min, sorted by Gaussian index, one CTA
+// per segment: each CTA looks at 32 tiles at a time (one warp reads their
+// offsets), collects the long ones in shared memory and sorts them in turn.
+__global__ void __launch_bounds__(256) k_segsort_long(unsigned int* vals, unsigned int* tmp,
+                                                      const unsigned long long* toff, int T,
+                                                      const DevStatus* st, int64_t m_cap,
+                                                      int sort_min) {
+  __shared__ unsigned int sh[SEG_BIG_CHUNK];
+  __shared__ int s_long[32];
+  __shared__ int s_n;
+  for (int t0 = blockIdx.x * 32; t0 < T; t0 += gridDim.x * 32) {
+    __syncthreads();  // the previous round is done with s_long
+    if (threadIdx.x < 32) {
+      const int t = t0 + (int)threadIdx.x;
+      int64_t a = 0, b = 0;
+      if (t < T) tile_segment(toff, t, T, st, m_cap, a, b);
+      const int L = (int)(b - a);
+      const unsigned m = __ballot_sync(FULL_MASK, t < T && L > 1 && L > sort_min);
+      if (m & (1u << threadIdx.x)) s_long[__popc(m & ((1u << threadIdx.x) - 1u))] = t;
+      if (threadIdx.x == 0) s_n = __popc(m);
     }
-    if (src != vals + a)
-      for (int i = threadIdx.x; i < L; i += blockDim.x) vals[a + i] = src[i];
     __syncthreads();
+    const int nl = s_n;
+    for (int q = 0; q < nl; ++q) sort_segment_cta(vals, tmp, toff, s_long[q], T, st, m_cap, sh);
   }
 }
 
@@ -732,7 +684,7 @@ cudaError_t run_binning(const PrepParams& p, int dtype, int T, unsigned long lon
   // wide Gaussian (up to WIDE_GRID at a time)
   const int64_t wt_blocks = (int64_t)((p.tiles_x + WT_BLOCK - 1) / WT_BLOCK) *
                             ((p.tiles_y + WT_BLOCK - 1) / WT_BLOCK);
-  const unsigned wt_grid = (unsigned)std::max<int64_t>(wt_blocks, WIDE_GRID);
+  const unsigned wt_grid = (unsigned)std::max<int64_t>(wt_blocks, 148 * 4);
   if (batch) k_wide<true, true><<<WIDE_GRID, 256, 0, s>>>(p);
   else if (T > 0) k_wide_tiles<true><<<wt_grid, 256, 0, s>>>(p);
   // the tile scan; for one image its last pass also writes the tile ranges
@@ -754,7 +706,7 @@ cudaError_t run_binning(const PrepParams& p, int dtype, int T, unsigned long lon
   if ((e = launch_emit(p, s)) != cudaSuccess) return e;
   if (batch) k_wide<true, false><<<WIDE_GRID, 256, 0, s>>>(p);
   else if (T > 0) k_wide_tiles<false><<<wt_grid, 256, 0, s>>>(p);
-  if ((e = launch_segsort(p.vals, p.tmp, p.toff, T, p.status, p.m_cap, p.big, sort_min, s)) !=
+  if ((e = launch_segsort(p.vals, p.tmp, p.toff, T, p.status, p.m_cap, sort_min, s)) !=
       cudaSuccess)
     return e;
   if (!batch) return cudaGetLastError();
@@ -764,11 +716,10 @@ cudaError_t run_binning(const PrepParams& p, int dtype, int T, unsigned long lon
 
 cudaError_t launch_segsort(unsigned int* vals, unsigned int* tmp,
                            const unsigned long long* toff, int T, DevStatus* status,
-                           int64_t m_cap, int* big, int sort_min, cudaStream_t s) {
+                           int64_t m_cap, int sort_min, cudaStream_t s) {
   if (T == 0) return cudaSuccess;
-  const unsigned grid = (unsigned)std::min<int64_t>((T + 255) / 256, 148 * 4);
-  k_segsort<<<grid, 256, 0, s>>>(vals, toff, T, status, m_cap, big, sort_min);
-  k_segsort_big<<<148 * 8, 256, 0, s>>>(vals, tmp, toff, T, status, m_cap, big);
+  const unsigned grid = (unsigned)std::min<int64_t>(((int64_t)T + 31) / 32, 148 * 8);
+  k_segsort_long<<<grid, 256, 0, s>>>(vals, tmp, toff, T, status, m_cap, sort_min);
   return cudaGetLastError();
 }
 

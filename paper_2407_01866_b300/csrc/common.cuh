@@ -46,7 +46,7 @@ struct DevStatus {
   unsigned long long m_needed;  // total intersections M
   unsigned long long evals;     // sum_j |S_j| * pixels(j)
   double loss_sum;              // sum |c_r - c_t| of the fused backward
-  unsigned int big_cnt;         // tiles whose list is sorted by whole CTAs
+  unsigned int reserved2;
   unsigned int wide_cnt;        // Gaussians whose tile box is binned by whole CTAs
   unsigned int pad[6];
 };

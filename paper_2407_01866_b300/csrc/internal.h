@@ -16,8 +16,7 @@ constexpr int SCAN_ITEMS = SCAN_THREADS * SCAN_PER_THREAD;
 
 // Byte offsets of the workspace sections (all 256-byte aligned).
 struct WsLayout {
-  size_t status, rec, trig, color, rec16, col16, tcnt, toff, part, vals, tmp, big, wide, wide_geo,
-      range;
+  size_t status, rec, trig, color, rec16, col16, tcnt, toff, part, vals, tmp, wide, wide_geo, range;
   size_t total;
   int64_t part_len;     // scan partials entries
   int tiles_x, tiles_y;
@@ -47,7 +46,6 @@ struct PrepParams {
   unsigned long long* toff;     // [T] start of each tile's segment
   unsigned int* vals;           // [m_cap] Gaussian index per intersection
   unsigned int* tmp;            // [m_cap] merge buffer of long segments
-  int* big;                     // [T] tiles whose segment is sorted by a CTA
   int* wide;                    // [N] Gaussians whose tile box is binned by a CTA
   float4* wide_geo;             // [N] their (mx, my, r, index bits), same order
   int64_t m_cap;
@@ -114,7 +112,7 @@ cudaError_t launch_scan_u32_to_u64(const unsigned int* in, unsigned long long* o
 // Sorts every tile segment longer than sort_min by Gaussian index.
 cudaError_t launch_segsort(unsigned int* vals, unsigned int* tmp,
                            const unsigned long long* toff, int T, DevStatus* status,
-                           int64_t m_cap, int* big, int sort_min, cudaStream_t s);
+                           int64_t m_cap, int sort_min, cudaStream_t s);
 cudaError_t launch_ranges(const unsigned long long* toff, int2* range, int T, int64_t m_cap,
                           int H, int W, int tile, int tiles_x, DevStatus* status,
                           cudaStream_t s);
