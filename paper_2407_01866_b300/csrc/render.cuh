@@ -28,8 +28,9 @@
 //   blend   the winners' slots come out of pass A: their keys are recomputed
 //           exactly and blended with w = exp(-(q - q_min)/2) (Eq. 5). The
 //           adjoint also records each winner as (slot, rank of the pixel
-//           among this warp's pixels that won the slot), from per-warp lane
-//           masks of every slot's winners.
+//           among this warp's pixels that won the slot): each pixel ORs its
+//           lane bit into its warp's mask of the slot, and the rank is the
+//           number of bits set before its own.
 //   pass C  (adjoint only) a counting sort of those records lays out the
 //           winning (candidate, pixel) pairs candidate-major; the pairs are
 //           split evenly over the CTA's threads; each accumulates dL/dq
@@ -785,66 +786,6 @@ __device__ __forceinline__ void exact_winners(const RenderParams& p, int cnt, fl
   }
 }
 
-// Eq. 5 over the winners whose slots are in tq: their keys are recomputed
-// exactly, q_min is the smallest of them, and the winners are blended in the
-// packed order with w = exp(-(q - q_min)/2). ALL: every entry of tq holds a
-// winner (lists of at least K entries), so no entry is tested. REC: each
-// winner of a live pixel also sets the lane's bit in its warp's mask of the
-// slot (cnt_w), for pass C's records.
-template <int K, int NC, int CH, bool ALL, bool REC>
-__device__ __forceinline__ void blend_winners(const RenderParams& p, float px, float py,
-                                              const int (&tq)[K], bool live,
-                                              const float4* s_a, const float2* s_b,
-                                              const float* s_col, unsigned* cnt_w,
-                                              PixelBlend<Chan<NC>::R>& r) {
-  constexpr int NCR = Chan<NC>::R;
-  const int n = nchan<NC>(p);
-  const unsigned bit = 1u << (threadIdx.x & 31);
-  float qe[K];
-  float q0 = F_INF;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (ALL || tq[k] != PK_NONE) {
-      const int j = tq[k] & 0xff;
-      if (REC && live) atomicOr(&cnt_w[j], bit);
-      const float4 a = s_a[j];
-      qe[k] = rank_key(px, py, a.x, a.y, a.z, a.w, s_b[j].x);
-      q0 = fminf(q0, qe[k]);
-    }
-  }
-  r.q0 = p.normalize ? q0 : 0.0f;
-  r.Z = 0.0f;
-#pragma unroll
-  for (int c = 0; c < NCR; ++c) r.cr[c] = 0.0f;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (ALL || tq[k] != PK_NONE) {
-      const float w = blend_weight(r.q0, qe[k]);  // exactly 1 at q = q_min
-      r.Z += w;
-      float cc[NCR];
-      staged_colours<CH, NC>(p, s_col, s_b, tq[k] & 0xff, cc);
-#pragma unroll
-      for (int c = 0; c < NCR; ++c)
-        if (NC > 0 || c < n) r.cr[c] = fmaf(w, cc[c], r.cr[c]);
-    }
-  }
-  r.iz = p.normalize ? (r.Z > 0.0f ? rcp_approx(r.Z) : 0.0f) : 1.0f;
-#pragma unroll
-  for (int c = 0; c < NCR; ++c) r.cr[c] *= r.iz;
-  r.tau = F_INF;
-  r.gcut = GID_NONE;
-}
-
-// Pass C's record of the k-th winner of a live pixel, once every lane of the
-// warp has set its bits (cnt_w): (slot << 5) | number of lower lanes that won
-// the slot; the number of the slot's winning pixels in the warp is the
-// popcount of its mask.
-__device__ __forceinline__ int winner_record(int pk, const unsigned* cnt_w) {
-  const int j = pk & 0xff;
-  const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
-  return (j << 5) | __popc(cnt_w[j] & lt);
-}
-
 // A pixel's winner records for pass C, in registers: one per register, or
 // (PACK, where registers are scarcer) two 16-bit records per register.
 template <int A, bool PACK>
@@ -859,6 +800,62 @@ struct WinRecs {
     return PACK ? (((unsigned)v[k >> 1] >> ((k & 1) * 16)) & 0xffffu) : (unsigned)v[k];
   }
 };
+
+// Eq. 5 over the winners whose slots are in tq: their keys are recomputed
+// exactly, q_min is the smallest of them, and the winners are blended in the
+// packed order with w = exp(-(q - q_min)/2). ALL: every entry of tq holds a
+// winner (lists of at least K entries), so no entry is tested. REC: each
+// winner of a live pixel also sets the lane's bit in its warp's mask of the
+// slot (cnt_w), and ew receives pass C's record of the k-th winner,
+// (slot << 5) | the number of the warp's lanes that set the mask before it
+// (the popcount of the mask the OR returns: unique, in no fixed order).
+template <int K, int NC, int CH, bool ALL, bool REC, bool PACK>
+__device__ __forceinline__ void blend_winners(const RenderParams& p, float px, float py,
+                                              const int (&tq)[K], bool live,
+                                              const float4* s_a, const float2* s_b,
+                                              const float* s_col, unsigned* cnt_w,
+                                              PixelBlend<Chan<NC>::R>& r,
+                                              WinRecs<K, PACK>* ew) {
+  constexpr int NCR = Chan<NC>::R;
+  const int n = nchan<NC>(p);
+  const unsigned bit = 1u << (threadIdx.x & 31);
+  float qe[K];
+  float q0 = F_INF;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (ALL || tq[k] != PK_NONE) {
+      const int j = tq[k] & 0xff;
+      const float4 a = s_a[j];
+      qe[k] = rank_key(px, py, a.x, a.y, a.z, a.w, s_b[j].x);
+      q0 = fminf(q0, qe[k]);
+    }
+  }
+  r.q0 = p.normalize ? q0 : 0.0f;
+  r.Z = 0.0f;
+#pragma unroll
+  for (int c = 0; c < NCR; ++c) r.cr[c] = 0.0f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (ALL || tq[k] != PK_NONE) {
+      const float w = blend_weight(r.q0, qe[k]);  // exactly 1 at q = q_min
+      if (REC) {
+        const int j = tq[k] & 0xff;
+        ew->set(k, live ? (j << 5) | __popc(atomicOr(&cnt_w[j], bit)) : 0);
+      }
+      r.Z += w;
+      float cc[NCR];
+      staged_colours<CH, NC>(p, s_col, s_b, tq[k] & 0xff, cc);
+#pragma unroll
+      for (int c = 0; c < NCR; ++c)
+        if (NC > 0 || c < n) r.cr[c] = fmaf(w, cc[c], r.cr[c]);
+    }
+  }
+  r.iz = p.normalize ? (r.Z > 0.0f ? rcp_approx(r.Z) : 0.0f) : 1.0f;
+#pragma unroll
+  for (int c = 0; c < NCR; ++c) r.cr[c] *= r.iz;
+  r.tau = F_INF;
+  r.gcut = GID_NONE;
+}
 
 // Where one tile of one image lives (the batched form renders many images).
 struct TileCtx {
@@ -896,10 +893,11 @@ __device__ __forceinline__ void fwd_tile(const RenderParams& p, const TileCtx& t
       if (__any_sync(FULL_MASK, in_img && pk_ambiguous(tk[K - 1], md)))
         exact_winners<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tk);
       if (len >= K)
-        blend_winners<K, NC, NT, true, false>(p, px, py, tk, in_img, s_a, s_b, s_col, nullptr, r);
+        blend_winners<K, NC, NT, true, false, false>(p, px, py, tk, in_img, s_a, s_b, s_col,
+                                                     nullptr, r, nullptr);
       else
-        blend_winners<K, NC, NT, false, false>(p, px, py, tk, in_img, s_a, s_b, s_col, nullptr,
-                                               r);
+        blend_winners<K, NC, NT, false, false, false>(p, px, py, tk, in_img, s_a, s_b, s_col,
+                                                      nullptr, r, nullptr);
     } else {
       float mdrop;
       culled_keys<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tq, mdrop);
@@ -1374,18 +1372,16 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
       if (__any_sync(FULL_MASK, in_img && pk_ambiguous(tk[K - 1], md)))
         exact_winners<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tk);
       if (len >= K)
-        blend_winners<K, NC, CH, true, true>(p, px, py, tk, in_img, s_a, s_b, s_col, cnt_w, r);
+        blend_winners<K, NC, CH, true, true, PACK>(p, px, py, tk, in_img, s_a, s_b, s_col,
+                                                   cnt_w, r, &ew);
       else
-        blend_winners<K, NC, CH, false, true>(p, px, py, tk, in_img, s_a, s_b, s_col, cnt_w, r);
-      __syncwarp();
-      // winners in ascending packed order: PK_NONE entries come last
+        blend_winners<K, NC, CH, false, true, PACK>(p, px, py, tk, in_img, s_a, s_b, s_col,
+                                                    cnt_w, r, &ew);
+      // winners in ascending packed order (PK_NONE entries come last): pass C
+      // reads the first nw records
       r.nw = 0;
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const bool ok = in_img && tk[k] != PK_NONE;
-        ew.set(k, ok ? winner_record(tk[k], cnt_w) : 0);
-        r.nw += ok ? 1 : 0;
-      }
+      for (int k = 0; k < K; ++k) r.nw += (in_img && tk[k] != PK_NONE) ? 1 : 0;
     } else {
       float mdrop;
       culled_keys<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tq, mdrop);
