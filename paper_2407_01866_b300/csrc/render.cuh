@@ -1051,11 +1051,13 @@ __device__ __forceinline__ int div_small(int a, int d, float inv) {
 }
 
 // Pass C of the fast path. The winning (candidate, pixel) pairs, in
-// (candidate, warp block, pixel) order, are first written out as a table of
-// 16-bit entries (candidate << 8 | pixel) by a counting sort of the winner
-// records (ew, in each pixel's registers): a scan over candidates of their
-// per-warp-block counts gives every (candidate, warp block) its first slot,
-// and each pixel stores its own winners at that slot plus its rank. The
+// (candidate, warp block) order, are first written out as a table of 16-bit
+// entries (candidate << 8 | pixel) by a counting sort of the winner records
+// (ew, in each pixel's registers): a scan over candidates of their
+// per-warp-block counts (the popcounts of the warps' slot masks) gives every
+// (candidate, warp block) its first slot, and each pixel stores its own
+// winners at that slot plus its rank (within a warp block, the order in which
+// the lanes' mask ORs were served). The
 // table is split into equal contiguous ranges, one per thread; a thread
 // accumulates the candidates of its range in registers. A candidate's partial
 // sums go to the candidate's slot A_j, written by the one thread whose range
