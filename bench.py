@@ -45,11 +45,11 @@ SM_MAX_MHZ = 2032.0
 # (profiles/k_render_fit2048_rgb.md has the command)
 FUSED_TRAFFIC_2048_RGB = 62_430_464
 TRAFFIC_STEPS_MAX = 50
-# library kernels of one fit step (the ncu launch list of the bench): finalize,
+# library kernels of one fit step (the ncu launch list of the bench):
 # preprocess, 2 wide-Gaussian passes, 3 scan passes (the last also writes the
 # tile ranges and the evaluation count), emit, the sort of long lists, fused
-# adjoint, Adam
-KERNELS_PER_FIT_STEP = 11
+# adjoint, Adam (whose last CTA also advances the step and writes the loss)
+KERNELS_PER_FIT_STEP = 10
 # the SSIM term adds the forward render and the one-pass image loss
 SSIM_EXTRA_KERNELS = 2
 

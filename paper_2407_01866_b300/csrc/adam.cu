@@ -17,6 +17,18 @@ __device__ __forceinline__ float one_minus_pow(float omb, int t) {
   return -expm1f((float)t * log1pf(-omb));
 }
 
+// The fit step's finalisation by the Adam launch's last CTA to finish: every
+// CTA has read *a.step (at its start) before it counts itself done, so the
+// increment is seen by none of them. fin->adam_done starts at 0 (binning
+// resets the status block every step).
+__device__ __forceinline__ void finalize_last(const AdamParams& a) {
+  __syncthreads();  // every thread of this CTA has read *a.step
+  if (threadIdx.x == 0 && atomicAdd(&a.fin->adam_done, 1u) == gridDim.x - 1) {
+    *a.step += 1;
+    if (a.fin_loss) *a.fin_loss = (float)(a.fin->loss_sum * (double)a.fin_inv_count);
+  }
+}
+
 // One thread per Gaussian row: the column of each element (and so its learning
 // rate and clamp) is known without a division, and a row's 5+n floats are
 // contiguous, so a warp touches 32 consecutive rows.
@@ -46,6 +58,7 @@ __global__ void __launch_bounds__(256) k_adam(AdamParams a) {
       a.v[i] = v;
     }
   }
+  if (a.fin) finalize_last(a);
 }
 
 // Rows of a multiple of 4 floats: consecutive threads take consecutive float4
@@ -85,6 +98,7 @@ __global__ void __launch_bounds__(256) k_adam_v4(AdamParams a) {
     M4[q] = m;
     V4[q] = v;
   }
+  if (a.fin) finalize_last(a);
 }
 
 __global__ void k_finalize(int32_t* step, DevStatus* st, float inv_count, float* loss_out) {
@@ -113,7 +127,10 @@ cudaError_t launch_finalize_batch(int32_t* step, const double* loss, const int4*
 }
 
 cudaError_t launch_adam(const AdamParams& a, cudaStream_t s) {
-  if (a.N == 0) return cudaSuccess;
+  if (a.N == 0) {  // no update; a fit step still advances
+    if (a.fin) k_finalize<<<1, 32, 0, s>>>(a.step, a.fin, a.fin_inv_count, a.fin_loss);
+    return cudaGetLastError();
+  }
   int64_t blocks = (a.N + 255) / 256;
   if (blocks > 148 * 16) blocks = 148 * 16;
   switch (a.n) {
@@ -173,12 +190,6 @@ cudaError_t launch_round_params(const float* src, void* dst, bool bf16, int64_t 
   else
     k_round_params<__half><<<(unsigned)blocks, 256, 0, s>>>(src, static_cast<__half*>(dst),
                                                             count);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_finalize(int32_t* step, DevStatus* status, float inv_count, float* loss_out,
-                            cudaStream_t s) {
-  k_finalize<<<1, 32, 0, s>>>(step, status, inv_count, loss_out);
   return cudaGetLastError();
 }
 

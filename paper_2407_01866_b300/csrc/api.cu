@@ -350,35 +350,56 @@ int igs_render_backward(const igs_gaussians* g, const igs_bins* bins, const igs_
   return IGS_OK;
 }
 
-int igs_adam_update(const igs_fit_state* st, const igs_config* cfg, igs_stream stream) {
+static int adam_params(const igs_fit_state* st, const igs_config* cfg, AdamParams* a) {
   if (!st || !st->params || !st->grad || !st->adam_m || !st->adam_v || !st->step)
     return fail(IGS_ERR_INVALID_ARG, "fit state has a NULL pointer");
   if (!cfg) return fail(IGS_ERR_INVALID_ARG, "config is NULL");
   if (st->N < 0 || st->n < 1 || st->n > 32)
     return fail(IGS_ERR_INVALID_ARG, "fit state sizes out of range");
+  a->P = st->params;
+  a->G = st->grad;
+  a->m = st->adam_m;
+  a->v = st->adam_v;
+  a->step = st->step;
+  a->N = st->N;
+  a->n = st->n;
+  a->lr_mu = cfg->lr_mu;
+  a->lr_theta = cfg->lr_theta;
+  a->lr_t = cfg->lr_inv_scale;
+  a->lr_c = cfg->lr_color;
+  a->b1 = (float)cfg->beta1;
+  a->b2 = (float)cfg->beta2;
+  a->omb1 = (float)(1.0 - cfg->beta1);
+  a->omb2 = (float)(1.0 - cfg->beta2);
+  a->eps = cfg->eps;
+  a->theta_min = cfg->theta_min;
+  a->theta_max = cfg->theta_max;
+  a->t_min = cfg->t_min;
+  a->t_max = cfg->t_max;
+  a->mu_min = cfg->mu_min;
+  a->mu_max = cfg->mu_max;
+  a->fin = nullptr;
+  a->fin_inv_count = 0.0f;
+  a->fin_loss = nullptr;
+  return IGS_OK;
+}
+
+int igs_adam_update(const igs_fit_state* st, const igs_config* cfg, igs_stream stream) {
   AdamParams a;
-  a.P = st->params;
-  a.G = st->grad;
-  a.m = st->adam_m;
-  a.v = st->adam_v;
-  a.step = st->step;
-  a.N = st->N;
-  a.n = st->n;
-  a.lr_mu = cfg->lr_mu;
-  a.lr_theta = cfg->lr_theta;
-  a.lr_t = cfg->lr_inv_scale;
-  a.lr_c = cfg->lr_color;
-  a.b1 = (float)cfg->beta1;
-  a.b2 = (float)cfg->beta2;
-  a.omb1 = (float)(1.0 - cfg->beta1);
-  a.omb2 = (float)(1.0 - cfg->beta2);
-  a.eps = cfg->eps;
-  a.theta_min = cfg->theta_min;
-  a.theta_max = cfg->theta_max;
-  a.t_min = cfg->t_min;
-  a.t_max = cfg->t_max;
-  a.mu_min = cfg->mu_min;
-  a.mu_max = cfg->mu_max;
+  if (int r = adam_params(st, cfg, &a)) return r;
+  IGS_CUDA(launch_adam(a, reinterpret_cast<cudaStream_t>(stream)), "adam");
+  return IGS_OK;
+}
+
+// A fit step's Adam update, whose last CTA also advances the step counter and
+// writes the mean loss (the finalisation).
+static int adam_and_finalize(const igs_fit_state* st, const igs_config* cfg, void* status,
+                             int32_t H, int32_t W, float* d_loss_out, igs_stream stream) {
+  AdamParams a;
+  if (int r = adam_params(st, cfg, &a)) return r;
+  a.fin = static_cast<DevStatus*>(status);
+  a.fin_inv_count = (float)(1.0 / ((double)H * W * st->n));
+  a.fin_loss = d_loss_out;
   IGS_CUDA(launch_adam(a, reinterpret_cast<cudaStream_t>(stream)), "adam");
   return IGS_OK;
 }
@@ -411,12 +432,7 @@ int igs_fit_step(const igs_fit_state* st, const float* d_target, int32_t H, int3
   if (int r = fit_loss_adjoint(&g, &bins, cfg, d_target, st->grad, static_cast<char*>(ws),
                                binning_bytes, stream))
     return r;
-  if (int r = igs_adam_update(st, cfg, stream)) return r;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  IGS_CUDA(launch_finalize(st->step, static_cast<DevStatus*>(bins.status),
-                           (float)(1.0 / ((double)H * W * st->n)), d_loss_out, s),
-           "finalize");
-  return IGS_OK;
+  return adam_and_finalize(st, cfg, bins.status, H, W, d_loss_out, stream);
 }
 
 int igs_fit_step_half(const igs_fit_state* st, void* d_params_half, int32_t half_dtype,
@@ -457,10 +473,7 @@ int igs_fit_step_half(const igs_fit_state* st, void* d_params_half, int32_t half
   if (int r = fit_loss_adjoint(&g, &bins, cfg, d_target, st->grad, static_cast<char*>(ws),
                                binning_bytes, stream))
     return r;
-  if (int r = igs_adam_update(st, cfg, stream)) return r;
-  IGS_CUDA(launch_finalize(st->step, static_cast<DevStatus*>(bins.status),
-                           (float)(1.0 / ((double)H * W * st->n)), d_loss_out, s),
-           "finalize");
+  if (int r = adam_and_finalize(st, cfg, bins.status, H, W, d_loss_out, stream)) return r;
   IGS_CUDA(launch_round_params(st->params, d_params_half, bf16, count, s), "round to half");
   return IGS_OK;
 }

@@ -42,7 +42,7 @@ __device__ __forceinline__ float half_bits_to_f32(unsigned short h, int hdt) {
 // have the layout of igs_stats in include/imgs.h.
 struct DevStatus {
   unsigned int flags;
-  unsigned int reserved;
+  unsigned int adam_done;       // CTAs of a fit step's Adam launch that are done
   unsigned long long m_needed;  // total intersections M
   unsigned long long evals;     // sum_j |S_j| * pixels(j)
   double loss_sum;              // sum |c_r - c_t| of the fused backward

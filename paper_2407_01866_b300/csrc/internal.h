@@ -145,6 +145,11 @@ struct AdamParams {
   int n;
   float lr_mu, lr_theta, lr_t, lr_c, b1, b2, omb1, omb2, eps;
   float theta_min, theta_max, t_min, t_max, mu_min, mu_max;
+  // a fit step's finalisation, done by the launch's last CTA (fin == nullptr:
+  // none): *step += 1 and *fin_loss = fin->loss_sum * fin_inv_count
+  DevStatus* fin;
+  float fin_inv_count;
+  float* fin_loss;
 };
 cudaError_t launch_adam(const AdamParams& a, cudaStream_t s);
 
@@ -187,8 +192,6 @@ cudaError_t launch_scan_u64(const unsigned long long* in, unsigned long long* ou
 // dst[i] = float16 (or bfloat16 if bf16) rounding of src[i], nearest even.
 cudaError_t launch_round_params(const float* src, void* dst, bool bf16, int64_t count,
                                 cudaStream_t s);
-cudaError_t launch_finalize(int32_t* step, DevStatus* status, float inv_count, float* loss_out,
-                            cudaStream_t s);
 // Batched form: step counter and per-image mean L1 loss.
 cudaError_t launch_finalize_batch(int32_t* step, const double* loss, const int4* dims, int B,
                                   int n, float* loss_out, cudaStream_t s);
