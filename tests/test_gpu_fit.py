@@ -108,6 +108,30 @@ def test_fit_step_matches_oracle_step():
     assert (np.abs(got - Pr) <= bound).all()
 
 
+def test_fit_step_counter_and_loss_without_gaussians():
+    """The step counter and the mean loss are written by the Adam launch's last
+    CTA, or by a separate kernel when there is nothing to update (N = 0); with
+    no Gaussians every pixel renders 0 and the loss is mean |c_t|."""
+    H, W, n = 40, 56, 3
+    target = synth.target_image(H, W, n, seed=4)
+    cfg = L.default_config()
+    for N in (0, 500):
+        P = synth.packed(synth.gaussians(max(N, 1), n, 5))
+        st = State(P)
+        st.c.N = N
+        ws = L.alloc_workspace(L.workspace_size(N, n, H, W, cfg, 8 * max(N, 1)))
+        loss = torch.zeros(1, device="cuda")
+        tt = dev(target)
+        for k in range(3):
+            L.fit_step(st.c, tt, H, W, cfg, ws, 8 * max(N, 1), loss)
+            torch.cuda.synchronize()
+            assert int(st.step.item()) == k + 1
+            if N == 0:
+                assert abs(loss.item() - float(np.abs(target.astype(np.float64)).mean())) <= 1e-6
+            else:
+                assert 0.0 < loss.item() < 1.0
+
+
 def test_fit_loss_decreases_and_graph_replay_matches_eager():
     H, W, N, n = 256, 256, 4096, 3
     d = synth.gaussians(N, n, 0)
