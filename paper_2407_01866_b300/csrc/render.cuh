@@ -55,6 +55,12 @@ namespace igs {
 // K = 0 selects all of S_j (no top-K): arrays keep one slot.
 template <int K> struct KS { static constexpr int A = K > 0 ? K : 1; };
 
+// Pass C's winner masks: for each warp block and staged candidate j, one
+// 32-bit word that lanes 0-15 set their bits in (at warp * CH + j) and one for
+// lanes 16-31 (rec_upper(NWB, CH) words further on, in the bank 16 away), so
+// that at most 16 lanes' atomics meet at one address.
+__host__ __device__ constexpr int rec_upper(int nwb, int ch) { return nwb * ch + 16; }
+
 template <int NC> struct Chan { static constexpr int R = NC; };
 template <> struct Chan<0> { static constexpr int R = 32; };  // runtime n <= 32
 
@@ -805,10 +811,11 @@ struct WinRecs {
 // exactly, q_min is the smallest of them, and the winners are blended in the
 // packed order with w = exp(-(q - q_min)/2). ALL: every entry of tq holds a
 // winner (lists of at least K entries), so no entry is tested. REC: each
-// winner of a live pixel also sets the lane's bit in its warp's mask of the
-// slot (cnt_w), and ew receives pass C's record of the k-th winner,
-// (slot << 5) | the number of the warp's lanes that set the mask before it
-// (the popcount of the mask the OR returns: unique, in no fixed order).
+// winner of a live pixel also sets the lane's bit in its half-warp's mask of
+// the slot (cnt_w: this lane's half's masks, as rec_upper describes), and ew
+// receives pass C's record of the k-th winner, (slot << 5) | the number of
+// lanes of its half that set the mask before it (the popcount of the value
+// the OR returns: unique within the half, in no fixed order).
 template <int K, int NC, int CH, bool ALL, bool REC, bool PACK>
 __device__ __forceinline__ void blend_winners(const RenderParams& p, float px, float py,
                                               const int (&tq)[K], bool live,
@@ -955,8 +962,12 @@ __host__ __device__ inline BwdSmem bwd_smem(int NT, int n, int CH) {
   L.ps0 = o;    o += 4 * NT;              // float4 (px, py, q0, beta) per pixel
   L.gh = o;     o = al4(o + col_stride(n) * NT);  // per-pixel -g/(2Z) (16-byte aligned)
   // pass C per-candidate sums A_j; before them (ex, ey) of the staged
-  // candidates, followed by pass B's NWB x CH counts (2 + NWB <= 10 <= 2 np
-  // words per candidate, as np >= 6 and CH <= NT, so they end inside slot_b)
+  // candidates, followed by pass B's winner masks of lanes 0-15 (NWB CH
+  // words, later the first slots: they end inside slot_a and slot_b, 2 + NWB
+  // <= 10 <= 2 np words per candidate as np >= 6 and CH <= NT) and, 16 words
+  // on, those of lanes 16-31 (at most 18 CH + 16 words from slot_a in all:
+  // inside slot_a, slot_b and win, at least 6 CH + 14 NT words; win is free
+  // until pass C's table is written, after these masks are last read)
   L.slot_a = o; o = al4(o + np * CH);
   L.slot_b = o; o = al4(o + np * NT);     // pass C per-thread sums B_t; rank keys before
   // pass C's table of 16-bit (candidate, pixel) pairs (<= 16 NT entries);
@@ -1054,10 +1065,11 @@ __device__ __forceinline__ int div_small(int a, int d, float inv) {
 // (candidate, warp block) order, are first written out as a table of 16-bit
 // entries (candidate << 8 | pixel) by a counting sort of the winner records
 // (ew, in each pixel's registers): a scan over candidates of their
-// per-warp-block counts (the popcounts of the warps' slot masks) gives every
-// (candidate, warp block) its first slot, and each pixel stores its own
-// winners at that slot plus its rank (within a warp block, the order in which
-// the lanes' mask ORs were served). The
+// per-half-warp counts (the popcounts of the half-warps' slot masks) gives
+// every (candidate, half of a warp block) its first slot (both halves' as
+// 16-bit fields of the lower half's mask word), and each pixel stores its own
+// winners at that slot plus its rank (within a half, the order in which the
+// lanes' mask ORs were served). The
 // table is split into equal contiguous ranges, one per thread; a thread
 // accumulates the candidates of its range in registers. A candidate's partial
 // sums go to the candidate's slot A_j, written by the one thread whose range
@@ -1079,30 +1091,42 @@ __device__ __forceinline__ void flat_pass_c(const RenderParams& p, const TileCtx
   constexpr int NCR = Chan<NC>::R;
   constexpr int A = KS<K>::A;
   const int n = nchan<NC>(p);
+  constexpr int U = rec_upper(NWB, CH);
+  static_assert(16 * NT < 65536, "first slots are 16-bit fields");
   const int tid = threadIdx.x;
-  // candidate tid's counts per warp block
-  int pre[NWB];
+  // candidate tid's counts per half of each warp block (words wb CH + tid and
+  // U + wb CH + tid). Thread tid alone reads these words and then overwrites
+  // the first (with the first slots), so the counts can be read again after
+  // the scan.
   int tot = 0;
+  if (tid < cnt) {
 #pragma unroll
-  for (int wb = 0; wb < NWB; ++wb) {
-    pre[wb] = tot;
-    if (tid < cnt) tot += __popc(s_cnt[wb * CH + tid]);
+    for (int wb = 0; wb < NWB; ++wb)
+      tot += __popc(s_cnt[wb * CH + tid]) + __popc(s_cnt[U + wb * CH + tid]);
   }
   int P;
   const int base = block_scan_int<NWB>(tid < cnt ? tot : 0, s_scan, P);
   if (tid < cnt) {
+    int run = base;
 #pragma unroll
-    for (int wb = 0; wb < NWB; ++wb) s_cnt[wb * CH + tid] = (unsigned)(base + pre[wb]);
+    for (int wb = 0; wb < NWB; ++wb) {
+      const int lo = __popc(s_cnt[wb * CH + tid]);
+      const int hi = __popc(s_cnt[U + wb * CH + tid]);
+      s_cnt[wb * CH + tid] = (unsigned)run | ((unsigned)(run + lo) << 16);
+      run += lo + hi;
+    }
     s_coff[tid] = base;
   }
   if (tid == 0) s_coff[cnt] = P;
   __syncthreads();
   unsigned short* s_pair = s_win;
-  const unsigned* s_first = s_cnt + (tid >> 5) * CH;  // first slot of (candidate, my warp block)
+  // first slots of (candidate, my warp block): my half's 16-bit field
+  const unsigned* s_first = s_cnt + (tid >> 5) * CH;
+  const unsigned half_sel = (tid & 16) ? 0x4432u : 0x4410u;  // high / low field, zero-extended
   auto put = [&](int k) {
     const unsigned rec = ew.get(k);
     const int j = (int)(rec >> 5);
-    s_pair[s_first[j] + (rec & 31u)] = (unsigned short)((j << 8) | tid);
+    s_pair[__byte_perm(s_first[j], 0u, half_sel) + (rec & 31u)] = (unsigned short)((j << 8) | tid);
   };
   if (__all_sync(FULL_MASK, nw == A)) {
 #pragma unroll
@@ -1366,8 +1390,13 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
     __syncthreads();
     const float4 R = block_rect<TILE>(t.x0, t.y0);
     if constexpr (K > 0) {
+      constexpr int U = rec_upper(NT / 32, CH);
       unsigned* cnt_w = s_cnt + (threadIdx.x >> 5) * CH;  // this warp's winner masks
-      for (int j = threadIdx.x & 31; j < len; j += 32) cnt_w[j] = 0u;
+      for (int j = threadIdx.x & 31; j < len; j += 32) {
+        cnt_w[j] = 0u;
+        cnt_w[U + j] = 0u;
+      }
+      cnt_w += (threadIdx.x & 16) ? U : 0;  // this lane's half's
       int tk[K];
       int md;
       packed_keys<K>(len, px, py, in_img, R, s_a, s_b, s_e, tk, md);
