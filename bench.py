@@ -41,9 +41,9 @@ SM_MAX_MHZ = 2032.0
 # DRAM bytes (read + write) of one fused forward + L1 + adjoint launch of the
 # current kernel on the 2048^2 RGB state the bench measures by default (20
 # steps from the initial parameters), from one ncu capture of that launch:
-# dram__bytes_read.sum 61,396,736 + dram__bytes_write.sum 1,033,728
+# dram__bytes_read.sum 61,402,880 + dram__bytes_write.sum 1,032,704
 # (profiles/k_render_fit2048_rgb.md has the command)
-FUSED_TRAFFIC_2048_RGB = 62_430_464
+FUSED_TRAFFIC_2048_RGB = 62_435_584
 TRAFFIC_STEPS_MAX = 50
 # library kernels of one fit step (the ncu launch list of the bench):
 # preprocess, 2 wide-Gaussian passes, 3 scan passes (the last also writes the
