@@ -556,26 +556,19 @@ __device__ __forceinline__ int tie_cutoff(int cnt, float px, float py, bool tie,
   return tie ? gc : GID_NONE;
 }
 
-// Pass B over the staged list: membership and blend. With REC (the fast
-// adjoint) it also records, for pass C, the winners of every live pixel: the
-// pixel's k-th winner goes to wrec[k * NT] as (staged index << 5 | rank of the
-// pixel among this warp's winning live pixels of that candidate), and the
-// number of such pixels of this warp goes to cnt_w[j] for every staged j.
-// A pixel has at most K winners (pass A's culling never drops a key <= tau),
-// so at most A records; the guard only keeps the stores in bounds.
-template <int K, int NC, int CH, int NT, bool REC>
+// Pass B over the staged list where there are no packed keys (K = 0, where
+// every candidate is kept): membership against (tau, tie cut-off) and blend.
+template <int K, int NC, int CH>
 __device__ __forceinline__ void culled_blend(const RenderParams& p, int cnt, float px, float py,
                                              bool live, const float4& R,
                                              const float (&tq)[KS<K>::A], float mdrop,
                                              const float4* s_a, const float2* s_b,
                                              const float2* s_e, const float* s_col,
-                                             unsigned* cnt_w, unsigned short* wrec,
                                              PixelBlend<Chan<NC>::R>& r) {
   constexpr int NCR = Chan<NC>::R;
   constexpr int A = KS<K>::A;
   const int n = nchan<NC>(p);
   const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;  // lanes below this one
   r.nw = 0;
   r.q0 = p.normalize ? tq[0] : 0.0f;
   r.tau = K == 0 ? F_INF : tq[A - 1];
@@ -593,19 +586,9 @@ __device__ __forceinline__ void culled_blend(const RenderParams& p, int cnt, flo
     const int jl = c0 + lane;
     const bool in = jl < cnt;
     const bool surv = in && !(key_lower_bound(s_a[jl], s_b[jl].x, s_e[jl], R) > T);
-    if (REC && in && !surv) cnt_w[jl] = 0u;
     unsigned m = __ballot_sync(FULL_MASK, surv);
     auto take = [&](int j, float q, int gid) {
       const bool win = q < r.tau || (q == r.tau && gid <= r.gcut);
-      if (REC) {
-        const bool rec = win && live && r.nw < A;
-        const unsigned bal = __ballot_sync(FULL_MASK, rec);
-        if (lane == 0) cnt_w[j] = __popc(bal);
-        if (rec) {
-          wrec[r.nw * NT] = (unsigned short)((j << 5) | __popc(bal & lt));
-          ++r.nw;
-        }
-      }
       if (win) {
         const float w = blend_weight(r.q0, q);  // exactly 1 at q = q_min
         r.Z += w;
@@ -908,8 +891,7 @@ __device__ __forceinline__ void fwd_tile(const RenderParams& p, const TileCtx& t
     } else {
       float mdrop;
       culled_keys<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tq, mdrop);
-      culled_blend<K, NC, NT, NT, false>(p, len, px, py, in_img, R, tq, mdrop, s_a, s_b, s_e,
-                                         s_col, nullptr, nullptr, r);
+      culled_blend<K, NC, NT>(p, len, px, py, in_img, R, tq, mdrop, s_a, s_b, s_e, s_col, r);
     }
   } else {
     select_keys<TILE, K, NT>(p, t.range, px, py, tq, s_a, s_b);
@@ -1416,8 +1398,7 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
     } else {
       float mdrop;
       culled_keys<K>(p, len, px, py, in_img, R, s_a, s_b, s_e, tq, mdrop);
-      culled_blend<K, NC, CH, NT, false>(p, len, px, py, in_img, R, tq, mdrop, s_a, s_b, s_e,
-                                         s_col, nullptr, nullptr, r);
+      culled_blend<K, NC, CH>(p, len, px, py, in_img, R, tq, mdrop, s_a, s_b, s_e, s_col, r);
     }
   } else {
     select_keys<TILE, K, CH>(p, t.range, px, py, tq, s_a, s_b);
