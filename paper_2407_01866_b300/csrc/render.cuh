@@ -1373,6 +1373,11 @@ __device__ __forceinline__ void bwd_tile(const RenderParams& p, const TileCtx& t
     const float4 R = block_rect<TILE>(t.x0, t.y0);
     if constexpr (K > 0) {
       constexpr int U = rec_upper(NT / 32, CH);
+      // the masks start 2 CH words into slot_a (np = 5 + n >= 6 words per
+      // candidate there, per pixel in slot_b; win holds 8 NT words): the lower
+      // half's end inside slot_a and slot_b, the upper half's inside win
+      static_assert(2 * CH + (NT / 32) * CH <= 6 * CH + 6 * NT, "lower masks outgrow the sums");
+      static_assert(2 * CH + U + (NT / 32) * CH <= 6 * CH + 14 * NT, "upper masks outgrow win");
       unsigned* cnt_w = s_cnt + (threadIdx.x >> 5) * CH;  // this warp's winner masks
       for (int j = threadIdx.x & 31; j < len; j += 32) {
         cnt_w[j] = 0u;
