@@ -28,9 +28,9 @@
 //   blend   the winners' slots come out of pass A: their keys are recomputed
 //           exactly and blended with w = exp(-(q - q_min)/2) (Eq. 5). The
 //           adjoint also records each winner as (slot, rank of the pixel
-//           among this warp's pixels that won the slot): each pixel ORs its
-//           lane bit into its warp's mask of the slot, and the rank is the
-//           number of bits set before its own.
+//           among its half-warp's pixels that won the slot): each pixel ORs
+//           its lane bit into its half-warp's mask of the slot, and the rank
+//           is the number of bits set before its own.
 //   pass C  (adjoint only) a counting sort of those records lays out the
 //           winning (candidate, pixel) pairs candidate-major; the pairs are
 //           split evenly over the CTA's threads; each accumulates dL/dq
